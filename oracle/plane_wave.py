@@ -1,0 +1,102 @@
+"""Closed-form discrete solution of the schemes for a periodic plane wave.
+
+TEST INFRASTRUCTURE ONLY (see the package docstring).
+
+On a periodic grid every stencil sum of Eq. notations2 maps a Fourier mode
+onto itself.  With theta = (k1 h, k2 h) the delta sums have the symbols
+    delta(1,0) -> 2 cos th1 + 2 cos th2 - 4
+    delta(1,1) -> 4 cos th1 cos th2 - 4
+    delta(2,0) -> 2 cos 2th1 + 2 cos 2th2 - 4,
+so Lambda_a = a10 delta(1,0) + a11 delta(1,1) + a20 delta(2,0) has the symbol
+S_a (likewise S_b with the b coefficients of the first step).  Writing
+u^n = A_n cos(k.x) + B_n sin(k.x):
+* the first step (Eq. A1 in the forms comp5.1 / 9.1 / 13.1) gives
+  (A_1, B_1) = (1 + S_a/2)(A_0, B_0) + tau (1 + S_b)(C_0, D_0) for
+  v^0 = C_0 cos + D_0 sin;
+* the two-step (Eq. A2) gives X_{n+1} = (2 + S_a) X_n - X_{n-1}, whose
+  solution with cos(phi) = 1 + S_a/2 is
+  X_n = X_0 cos(n phi) + (X_1 - X_0 cos phi) sin(n phi) / sin(phi).
+The coefficients are the printed Section 6 ones, written here independently
+of the C oracle.  The result is exact up to rounding at any grid size, which
+makes it the reference for large grids and long runs.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+
+def section6_coeffs(scheme: int, lam: float, conventional: bool = False):
+    """(a10, a11, a20), (b10, b11, b20) of Section 6."""
+    l2 = lam * lam
+    if scheme == 5:
+        return (l2, 0.0, 0.0), ((0.0 if conventional else l2 / 6.0), 0.0, 0.0)
+    if scheme == 9:
+        if conventional:
+            return (2.0 * l2 / 3.0, l2 / 6.0, 0.0), (0.0, 0.0, 0.0)
+        return (l2 * (1 - l2 / 3), l2 * l2 / 6, 0.0), (l2 / 6 * (1 - l2 / 5), l2 * l2 / 60, 0.0)
+    if scheme == 13:
+        a = (l2 * (4 - 2 * l2) / 3, l2 * l2 / 6, l2 * (l2 - 1) / 12)
+        if conventional:
+            return a, (0.0, 0.0, 0.0)
+        return a, (l2 / 6 * (4 / 3 - 2 * l2 / 5), l2 * l2 / 60, l2 / 6 * (l2 / 20 - 1 / 12))
+    raise ValueError(f"unknown scheme {scheme}")
+
+
+def symbol(coef, th1: float, th2: float) -> float:
+    c1, c2 = math.cos(th1), math.cos(th2)
+    return (coef[0] * (2 * c1 + 2 * c2 - 4) + coef[1] * (4 * c1 * c2 - 4)
+            + coef[2] * (2 * math.cos(2 * th1) + 2 * math.cos(2 * th2) - 4))
+
+
+def _chebyshev_ratio(n: int, phi: float, cphi: float) -> float:
+    """sin(n phi) / sin(phi), continuous at sin(phi) = 0."""
+    s = math.sin(phi)
+    if abs(s) < 1e-7:
+        # U_{n-1}(cos phi) near phi = 0 or pi
+        sign = 1.0 if cphi > 0 else (-1.0) ** (n - 1)
+        return sign * n
+    return math.sin(n * phi) / s
+
+
+def amplitudes(scheme, lam, tau, k1, k2, h, n, a0=1.0, b0=0.0, c0=0.0, d0=None, c=1.0,
+               conventional=False):
+    """(A_n, B_n) of u^n = A_n cos(k.x) + B_n sin(k.x).
+
+    Defaults are the plane wave cos(k.x - c|k|t): u^0 = cos(k.x),
+    v^0 = c|k| sin(k.x)."""
+    if d0 is None:
+        d0 = c * math.hypot(k1, k2)
+    a, b = section6_coeffs(scheme, lam, conventional)
+    th1, th2 = k1 * h, k2 * h
+    sa, sb = symbol(a, th1, th2), symbol(b, th1, th2)
+    A1 = (1 + sa / 2) * a0 + tau * (1 + sb) * c0
+    B1 = (1 + sa / 2) * b0 + tau * (1 + sb) * d0
+    if n == 0:
+        return a0, b0
+    if n == 1:
+        return A1, B1
+    cphi = 1 + sa / 2
+    if abs(cphi) > 1.0:
+        raise ValueError("mode is outside the stability region")
+    phi = math.acos(cphi)
+    r = _chebyshev_ratio(n, phi, cphi)
+    cn = math.cos(n * phi)
+    return a0 * cn + (A1 - a0 * cphi) * r, b0 * cn + (B1 - b0 * cphi) * r
+
+
+def field(scheme, lam, tau, k1, k2, h, nx, ny, n, x_off=0.0, **kw) -> np.ndarray:
+    """u^n on the (ny, nx) node set x = (i + x_off) h."""
+    an, bn = amplitudes(scheme, lam, tau, k1, k2, h, n, **kw)
+    x1 = (np.arange(nx) + x_off) * h
+    x2 = (np.arange(ny) + x_off) * h
+    ph = k1 * x1[None, :] + k2 * x2[:, None]
+    return an * np.cos(ph) + bn * np.sin(ph)
+
+
+def sample(scheme, lam, tau, k1, k2, h, n, ii, jj, x_off=0.0, **kw) -> np.ndarray:
+    """u^n at the nodes (ii[m], jj[m])."""
+    an, bn = amplitudes(scheme, lam, tau, k1, k2, h, n, **kw)
+    ph = k1 * (np.asarray(ii) + x_off) * h + k2 * (np.asarray(jj) + x_off) * h
+    return an * np.cos(ph) + bn * np.sin(ph)
