@@ -1,0 +1,348 @@
+"""Benchmark: explicit time marching of the 2D wave equation on one GB300.
+
+Workload (one benchmark step): the 9-point and the 13-point scheme of
+arXiv:1904.04048 (Section 6), FP32 storage, 4096 x 4096 periodic grid,
+h = 1/4096, c = 1, lambda = 0.9 x each scheme's stability limit, 2000 time
+levels each (the first step, Eq. A1, then 1999 two-steps, Eq. A2), followed
+by an FP64 norm of the final field copied to the host.  Inputs: 16 seeded
+Gaussian pulses for u0 and band-limited random noise for v0 (seed 2019).
+
+Metric: point-updates per second (one point-update = one grid node advanced
+one time level), in units of 1e9.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs under torchrun with one rank per GPU; every rank runs the same
+workload on its own GPU (independent replicas, weak scaling) and the value
+is the total over ranks divided by the slowest rank's time.
+``--impl reference`` times the FP64 CPU oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N = 4096
+STEPS_PER_SCHEME = 2000
+SCHEMES = (9, 13)
+SEED = 2019
+METRIC = "G point-updates/s"
+WORKLOAD = ("9-point + 13-point schemes, FP32 storage, 4096^2 periodic grid, lambda = 0.9 lambda_max, "
+            "2000 time levels each (first step + 1999 two-steps), 16 Gaussian pulses + band-limited "
+            "noise (seed 2019), FP64 norm of the final field to host")
+
+# DRAM bytes (read + write) of one launch of the TMA two-step kernel at the
+# benchmark size, from an ncu capture of the same kernel source (see the
+# profiles directory).  Keyed by a hash of the kernel sources so that the
+# figure is dropped once the kernel changes.
+NCU_TRAFFIC = {}
+
+
+def kernel_source_hash() -> str:
+    hsh = hashlib.sha256()
+    for f in ("kernels.cuh", "stencil_ops.cuh"):
+        with open(os.path.join(ROOT, "paper_1904_04048_gb300", "csrc", f), "rb") as fh:
+            hsh.update(fh.read())
+    return hsh.hexdigest()[:16]
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = str(device_index)
+        try:
+            import torch
+            self.dev = "GPU-" + str(torch.cuda.get_device_properties(device_index).uuid)
+        except Exception:
+            pass
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", self.dev, f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# --------------------------------------------------------------- CPU oracle
+def time_oracle(u0, v0, budget_s: float):
+    """Time the FP64 oracle (as it stands) on a bounded sample of the
+    workload: both schemes on the full 4096^2 grid for a few time levels."""
+    import oracle
+    threads = oracle.set_threads(os.cpu_count() or 1)
+    h = 1.0 / N
+    from initial_data import LAMBDA_MAX
+    # probe one level per scheme, then size the sample to the budget
+    t0 = time.perf_counter()
+    for s in SCHEMES:
+        lam = 0.9 * LAMBDA_MAX[s]
+        oracle.run(s, u0, v0, lam, lam * h, 1, bc=oracle.BC_PERIODIC)
+    probe = time.perf_counter() - t0
+    levels = max(2, int(budget_s / max(probe, 1e-3)))
+    t0 = time.perf_counter()
+    for s in SCHEMES:
+        lam = 0.9 * LAMBDA_MAX[s]
+        oracle.run(s, u0, v0, lam, lam * h, levels, bc=oracle.BC_PERIODIC)
+    dt = time.perf_counter() - t0
+    pts = len(SCHEMES) * levels * N * N
+    return {"value": pts / dt / 1e9, "unit": METRIC, "cores": threads, "kind": "oracle",
+            "sample": f"both schemes on the full {N}^2 grid, {levels} time levels each "
+                      f"({pts:.3e} point-updates, {dt:.1f} s)"}
+
+
+# ----------------------------------------------------------------- GPU arm
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+
+    from initial_data import BC_PERIODIC, LAMBDA_MAX, pulses_and_noise
+    from paper_1904_04048_gb300 import wave2d as w
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    w.lib()
+    u0, v0 = pulses_and_noise(N, seed=SEED)
+    h = 1.0 / N
+    stream = torch.cuda.Stream(device=dev)
+    sims = {}
+    for s in SCHEMES:
+        lam = 0.9 * LAMBDA_MAX[s]
+        sims[s] = w.Wave2D(N, N, h, lam * h, scheme=s, bc=BC_PERIODIC, dtype=w.F32, stream=stream.cuda_stream)
+    kernel = sims[13].info().kernel
+    du0 = torch.from_numpy(u0).to(dev)
+    dv0 = torch.from_numpy(v0).to(dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 512 MiB > L2
+    torch.cuda.synchronize(dev)
+    results = {}
+
+    def one_step(timing=None):
+        with torch.cuda.stream(stream):
+            flush.zero_()  # evict the previous step's levels from L2
+        for s in SCHEMES:
+            sims[s].first_step(du0, dv0)
+            if timing is not None:
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+            sims[s].step_n(STEPS_PER_SCHEME - 1)
+            if timing is not None:
+                e1.record(stream)
+                timing.append((s, e0, e1))
+            results[s] = sims[s].error_vs_exact()  # FP64 norm -> host (synchronises)
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+
+    for _ in range(args.warmup):
+        one_step()
+    barrier()
+    timing = []
+    c0 = w.launch_count()
+    with ClockSampler(local_rank) as clk:
+        t_start = torch.cuda.Event(enable_timing=True)
+        t_end = torch.cuda.Event(enable_timing=True)
+        t_start.record(stream)
+        for _ in range(args.steps):
+            one_step(timing)
+        t_end.record(stream)
+        barrier()
+    launches = w.launch_count() - c0
+    elapsed = t_start.elapsed_time(t_end) / 1e3
+    stepn_s = sum(a.elapsed_time(b) for _, a, b in timing) / 1e3
+    n_two_step_launches = args.steps * len(SCHEMES) * (STEPS_PER_SCHEME - 1)
+
+    # end-to-end through the public API with host buffers (pinned), copies timed
+    pu0 = torch.from_numpy(u0).pin_memory()
+    pv0 = torch.from_numpy(v0).pin_memory()
+    barrier()
+    e2e_steps = max(1, args.steps)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        for s in SCHEMES:
+            sims[s].first_step(pu0, pv0)      # host -> device copy inside the call
+            sims[s].step_n(STEPS_PER_SCHEME - 1)
+            results[s] = sims[s].error_vs_exact()  # device -> host norms
+    barrier()
+    e2e_elapsed = time.perf_counter() - t0
+
+    if world > 1:
+        t = torch.tensor([elapsed, e2e_elapsed], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        elapsed, e2e_elapsed = t.tolist()
+    pts_step = len(SCHEMES) * STEPS_PER_SCHEME * N * N
+    value = world * args.steps * pts_step / elapsed / 1e9
+    e2e_value = world * e2e_steps * pts_step / e2e_elapsed / 1e9
+    for s in SCHEMES:
+        sims[s].close()
+    if rank != 0:
+        return None
+
+    peak, peak_src = measured_peaks()
+    avg_launch = stepn_s / n_two_step_launches
+    alg_bytes = 12 * N * N  # read u^k, read u^{k-1}, write u^{k+1} (FP32)
+    achieved = alg_bytes / avg_launch / 1e9
+    src_hash = kernel_source_hash()
+    traffic = NCU_TRAFFIC.get(src_hash)
+    line = {
+        "metric": METRIC, "value": round(value, 3), "unit": "G point-updates/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(elapsed / args.steps * 1e3, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "grid": N, "schemes": list(SCHEMES),
+                   "time_levels_per_scheme": STEPS_PER_SCHEME, "boundary": "periodic",
+                   "point_updates_per_step": pts_step, "l2_flush_between_steps": True,
+                   "two_step_kernel": {1: "simple", 2: "tma"}.get(kernel, str(kernel)),
+                   "parallelism": f"replicas x{world}"},
+        "roofline": {"bound": "hbm", "kernel": "k2_tma (two-step, FP32, 13/9-point)",
+                     "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "peak_source": peak_src,
+                     "algorithmic_bytes_per_launch": alg_bytes,
+                     "avg_launch_us": round(avg_launch * 1e6, 3), "traffic": traffic},
+        "e2e": {"value": round(e2e_value, 3), "unit": "G point-updates/s",
+                "h2d_bytes_per_step": len(SCHEMES) * 2 * 8 * N * N,
+                "d2h_bytes_per_step": len(SCHEMES) * (8 * 8 + 4)},
+        "gpu_launches": launches,
+        "clocks": clk.summary(),
+        "result_norms": {str(s): [results[s][0], results[s][1]] for s in SCHEMES},
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = time_oracle(u0, v0, args.cpu_budget)
+    return line
+
+
+def run_reference(args, rank):
+    """The FP64 CPU oracle, as it stands, on the host cores."""
+    if rank != 0:
+        return None
+    import oracle
+    from initial_data import LAMBDA_MAX, pulses_and_noise
+    u0, v0 = pulses_and_noise(N, seed=SEED)
+    threads = oracle.set_threads(os.cpu_count() or 1)
+    h = 1.0 / N
+    levels = args.ref_levels
+    def one():
+        for s in SCHEMES:
+            lam = 0.9 * LAMBDA_MAX[s]
+            oracle.run(s, u0, v0, lam, lam * h, levels, bc=oracle.BC_PERIODIC)
+    for _ in range(args.warmup):
+        one()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        one()
+    dt = time.perf_counter() - t0
+    pts = args.steps * len(SCHEMES) * levels * N * N
+    v = pts / dt / 1e9
+    sample = (f"each step: both schemes on the full {N}^2 grid for {levels} time levels "
+              f"(the full workload has {STEPS_PER_SCHEME})")
+    return {"impl": "reference", "metric": METRIC, "value": round(v, 5), "unit": "G point-updates/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(dt / args.steps * 1e3, 3), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "grid": N, "schemes": list(SCHEMES),
+                       "time_levels_per_scheme": levels, "boundary": "periodic"},
+            "cpu_baseline": {"value": round(v, 5), "unit": "G point-updates/s", "cores": threads,
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": round(v, 5), "unit": "G point-updates/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle time for cpu_baseline")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-levels", type=int, default=4, help="time levels per scheme per reference step")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if world != args.gpus:
+        args.gpus = world
+    if args.impl == "reference":
+        line = run_reference(args, rank)
+    else:
+        if world > 1:
+            import torch
+            torch.distributed.init_process_group("nccl")
+        line = run_ours(args, rank, world, local_rank)
+        if world > 1:
+            import torch
+            torch.distributed.destroy_process_group()
+    if line is not None:
+        print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

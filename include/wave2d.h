@@ -1,0 +1,222 @@
+/*
+ * wave2d: explicit time marching of the 2D acoustic wave equation with the
+ * 5-, 9- and 13-point schemes generated by Poisson's formula
+ * (N. Khutoryansky, arXiv:1904.04048), on one NVIDIA GB300 (sm_103a).
+ *
+ * Problem (Section 2, Eq. we1): u_tt = c^2 (u_x1x1 + u_x2x2), u(.,0) = u0,
+ * u_t(.,0) = v0, on a uniform grid of spacing h with time step tau and
+ * Courant number lambda = c tau / h (Eq. Courant).
+ *
+ * Time-stepping algorithm (Section 3):
+ *   first step  (Eq. A1):  u^1 = u^0 + tau v^0 + 1/2 Lambda_a(u^0) + tau Lambda_b(v^0)
+ *   two-step    (Eq. A2):  u^{k+1} = 2 u^k - u^{k-1} + Lambda_a(u^k),  k >= 1
+ * with Lambda_a(w) = a10 delta_w(1,0) + a11 delta_w(1,1) + a20 delta_w(2,0),
+ * delta_w(q1,q2) = the sum of w over the four 90-degree rotations of the
+ * offset (q1,q2) minus four times the centre (Eq. notations2), and the
+ * coefficients of Section 6 (Eq. comp5.1/5.2, comp9.1/9.2, comp13.1/13.2):
+ *   scheme 5:  a10 = l^2                    b10 = l^2/6
+ *   scheme 9:  a10 = l^2 (1 - l^2/3)        b10 = l^2/6 (1 - l^2/5)
+ *              a11 = l^4/6                  b11 = l^4/60
+ *   scheme 13: a10 = l^2 (4 - 2 l^2)/3      b10 = l^2/6 (4/3 - 2 l^2/5)
+ *              a11 = l^4/6                  b11 = l^4/60
+ *              a20 = l^2 (l^2 - 1)/12       b20 = l^2/6 (l^2/20 - 1/12)
+ * (l = lambda; all other coefficients zero).  WAVE2D_CONVENTIONAL selects the
+ * comparison schemes of Section 6: b = 0 (central-difference first step,
+ * Eq. comp5.1a, comp9.1b) and, for scheme 9, a10 = 2 l^2/3, a11 = l^2/6
+ * (Eq. comp9.2b).
+ *
+ * Stability (Eq. stability5, stability9, Section 6.3): lambda <= lambda_max
+ * with lambda_max = 1/sqrt2 (schemes 5, 13), sqrt((3 - sqrt3)/2) (scheme 9;
+ * the printed value is read this way), sqrt3/2 (conventional 9).
+ *
+ * Conventions of every function below
+ *   Fields are row-major nx-by-ny arrays of double: node (i, j), i along x1,
+ *   j along x2, at index j*nx + i.  Boundary (Section 6.1.2, Section 6.3):
+ *   WAVE2D_BC_ZERO     nodes outside the nx-by-ny set hold 0 at every level
+ *                      (the grid boundary condition u = 0 of Section 6.1.2,
+ *                      a zero ring of width 2 for scheme 13);
+ *   WAVE2D_BC_PERIODIC indices wrap modulo nx and ny (Section 6.3).
+ *   Errors: every int function returns WAVE2D_OK (0) or a negative status;
+ *   wave2d_last_error() then gives a message (thread-local).  Kernels run
+ *   asynchronously on the handle's stream; a device-side failure surfaces as
+ *   WAVE2D_ERR_CUDA at the next call that synchronises (sync, norms, state).
+ *   Ownership: the library owns all device memory of a handle (allocated at
+ *   create through the allocator hook, freed by destroy).  Input arrays are
+ *   copied before the call returns; outputs go to caller buffers.
+ *   Thread safety: a handle is used by one host thread at a time.
+ */
+#ifndef WAVE2D_H
+#define WAVE2D_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    WAVE2D_OK = 0,
+    WAVE2D_ERR_ARG = -1,       /* invalid argument                              */
+    WAVE2D_ERR_UNSTABLE = -2,  /* lambda above the scheme's stability limit     */
+    WAVE2D_ERR_OOM = -3,       /* device allocation failed                      */
+    WAVE2D_ERR_CUDA = -4,      /* CUDA runtime / kernel error                   */
+    WAVE2D_ERR_NONFINITE = -5, /* a norm found NaN or Inf in the field          */
+    WAVE2D_ERR_TIMEOUT = -6,   /* a bounded device-side wait gave up            */
+    WAVE2D_ERR_STATE = -7      /* call out of order (e.g. stepping before init) */
+};
+
+enum { WAVE2D_BC_ZERO = 0, WAVE2D_BC_PERIODIC = 1 };
+
+/* Storage / arithmetic type of the time levels.  The first step always
+ * computes in FP64 and rounds into the storage type; norms reduce in FP64.
+ * WAVE2D_F32X2 keeps each value as an unevaluated sum hi + lo of two floats
+ * (double-float arithmetic, about 48 significant bits). */
+enum { WAVE2D_F64 = 0, WAVE2D_F32 = 1, WAVE2D_F32X2 = 2 };
+
+/* grid.flags */
+enum {
+    WAVE2D_ALLOW_UNSTABLE = 1, /* accept lambda > lambda_max (for instability tests) */
+    WAVE2D_CONVENTIONAL = 2    /* comparison schemes: central-difference first step,
+                                  isotropic 9-point Laplacian (Eq. comp9.2b)        */
+};
+
+/* Exact solutions for wave2d_error_vs_exact / wave2d_track_error.
+ *   STANDING: amp sin(2 pi m x1) sin(2 pi m x2) sin(2 sqrt2 pi m c t)
+ *             (Eq. "exact sol" for amp = m = 1)
+ *   PLANE:    amp cos(k1 x1 + k2 x2 - c |k| t)
+ *   NONE:     u_e = 0 (the norms then measure the field itself)
+ * Node (i, j) sits at x = ((i + x_off) h, (j + x_off) h); the paper's
+ * Dirichlet node set {0 < i < n} is x_off = 1, its periodic one x_off = 0. */
+enum { WAVE2D_EXACT_NONE = 0, WAVE2D_EXACT_STANDING = 1, WAVE2D_EXACT_PLANE = 2 };
+
+typedef struct {
+    int32_t kind;
+    int32_t reserved;
+    double amp;
+    double m;      /* STANDING mode number */
+    double k1, k2; /* PLANE wave vector    */
+    double x_off;
+} wave2d_exact;
+
+typedef struct {
+    int32_t nx, ny; /* updated nodes along x1 and x2 (1 .. 65536 each)          */
+    int32_t bc;     /* WAVE2D_BC_*                                             */
+    int32_t dtype;  /* WAVE2D_F64 | WAVE2D_F32 | WAVE2D_F32X2                  */
+    int32_t flags;  /* WAVE2D_ALLOW_UNSTABLE | WAVE2D_CONVENTIONAL              */
+    int32_t reserved;
+    void *stream;   /* cudaStream_t the handle launches on; NULL = default stream */
+} wave2d_grid;
+
+typedef struct wave2d *wave2d_t;
+
+/* Kernel selection for the two-step.  Zero-initialised = automatic. */
+enum {
+    WAVE2D_KERNEL_AUTO = 0,
+    WAVE2D_KERNEL_SIMPLE = 1,   /* one thread per node, global loads            */
+    WAVE2D_KERNEL_TMA = 2,      /* TMA-staged shared-memory tiles, one step      */
+    WAVE2D_KERNEL_TEMPORAL = 3  /* TMA tiles advanced T steps in shared memory   */
+};
+
+typedef struct {
+    int32_t kernel;       /* WAVE2D_KERNEL_*                                      */
+    int32_t tile_h;       /* rows per tile (TMA kernels); 0 = default             */
+    int32_t temporal_t;   /* steps per launch for WAVE2D_KERNEL_TEMPORAL; 0 = auto */
+    int32_t use_graph;    /* capture runs of steps in a CUDA graph: 1 on, 0 off,
+                             -1 automatic                                         */
+} wave2d_tune;
+
+typedef struct {
+    double lambda, h, tau, c;
+    double a[3];     /* a10, a11, a20 as used (FP64)                          */
+    double b[3];     /* b10, b11, b20 as used (FP64)                          */
+    double lambda_max;
+    int64_t k;       /* index of the current time level u^k (0 before any step) */
+    int32_t scheme, radius, dtype, bc;
+    int32_t nx, ny, pitch, ghost;
+    int64_t device_bytes;
+    int32_t kernel;  /* two-step kernel currently selected (WAVE2D_KERNEL_*)  */
+    int32_t temporal_t;
+} wave2d_info_t;
+
+/* ------------------------------------------------------------------------ */
+/* Allocation hook (process-wide).  alloc returns a device pointer with at   */
+/* least 256-byte alignment or NULL; free releases it.  Passing NULL for both */
+/* restores cudaMalloc / cudaFree.  Handles keep the hook they were created   */
+/* with.                                                                      */
+/* ------------------------------------------------------------------------ */
+typedef void *(*wave2d_alloc_fn)(size_t bytes, void *stream, void *ctx);
+typedef void (*wave2d_free_fn)(void *ptr, size_t bytes, void *stream, void *ctx);
+int wave2d_set_allocator(wave2d_alloc_fn alloc, wave2d_free_fn release, void *ctx);
+
+/* Create a simulation of `scheme` (5, 9 or 13) on `grid` with spacing h,
+ * time step tau and speed c (Section 3; lambda = c tau / h, Eq. Courant).
+ * Allocates the two time levels (plus a halo ring) and the reduction scratch
+ * on the current device.  Errors: WAVE2D_ERR_ARG (bad sizes / scheme / h,
+ * tau, c not positive and finite), WAVE2D_ERR_UNSTABLE (lambda above
+ * lambda_max * (1 + 1e-12) without WAVE2D_ALLOW_UNSTABLE), WAVE2D_ERR_OOM. */
+int wave2d_create(const wave2d_grid *grid, double h, double tau, double c, int scheme,
+                  wave2d_t *out);
+
+/* First time step (Eq. A1 in the discrete forms comp5.1, comp9.1, comp13.1):
+ * u0, v0 are nx*ny FP64 arrays, in host memory (on_device = 0) or device
+ * memory (on_device = 1).  Computes u^1 in FP64 and stores u^0, u^1 in the
+ * storage type; afterwards k = 1.  Resets any spacetime error accumulation
+ * and, if tracking is on (wave2d_track_error), adds the k = 1 term. */
+int wave2d_first_step(wave2d_t h, const double *u0, const double *v0, int on_device);
+
+/* n two-steps (Eq. A2 in the forms comp5.2, comp9.2, comp13.2), in place,
+ * asynchronous on the handle's stream; k += n.  n = 0 is a no-op; n < 0 is
+ * WAVE2D_ERR_ARG; before first_step / set_state it is WAVE2D_ERR_STATE. */
+int wave2d_step_n(wave2d_t h, int64_t n);
+
+/* Error of the current level u^k against an exact solution at t = k tau,
+ * reduced in FP64 on the device:
+ *   rel_l2   = sqrt(sum (u - u_e)^2 / sum u_e^2)  (for kind NONE: sqrt(sum u^2))
+ *   rel_linf = max |u - u_e| / max |u_e|           (for kind NONE: max |u|)
+ * spacetime_E (may be NULL) receives the paper's relative space-time error
+ * E(n, n_t) of Eq. error, sum over k = 1..n_t, accumulated since first_step
+ * when tracking is enabled, else NaN.  Any output pointer may be NULL.
+ * Synchronises the stream.  Returns WAVE2D_ERR_NONFINITE (outputs still
+ * written) if the field holds NaN or Inf. */
+int wave2d_error_vs_exact(wave2d_t h, const wave2d_exact *ex, double *rel_l2, double *rel_linf,
+                          double *spacetime_E);
+
+/* Enable (ex != NULL) or disable (NULL) accumulation of the sums of Eq. error
+ * after every step from the next first_step on.  Tracking uses the one-node-
+ * per-thread kernel with the reduction fused into the step. */
+int wave2d_track_error(wave2d_t h, const wave2d_exact *ex);
+
+/* Checkpoint: copy u^{k-1}, u^k (as FP64; exact for FP64 and FP32 storage,
+ * hi + lo rounded to FP64 for FP32X2) and k to host buffers of nx*ny doubles.
+ * Any pointer may be NULL.  Synchronises. */
+int wave2d_get_state(wave2d_t h, double *u_prev, double *u_cur, int64_t *k);
+
+/* Resume: load u^{k-1}, u^k (host or device FP64 arrays, rounded to the
+ * storage type) and the level index k (k >= 1). */
+int wave2d_set_state(wave2d_t h, const double *u_prev, const double *u_cur, int64_t k,
+                     int on_device);
+
+/* Raw storage copy of the two current levels to host memory, for bitwise
+ * checkpoints in every storage type.  bytes must be >= wave2d_raw_bytes(). */
+int64_t wave2d_raw_bytes(wave2d_t h);
+int wave2d_get_raw(wave2d_t h, void *dst, int64_t bytes, int64_t *k);
+int wave2d_set_raw(wave2d_t h, const void *src, int64_t bytes, int64_t k);
+
+int wave2d_set_tuning(wave2d_t h, const wave2d_tune *tune);
+int wave2d_get_info(wave2d_t h, wave2d_info_t *info);
+int wave2d_sync(wave2d_t h);
+void wave2d_destroy(wave2d_t h);
+const char *wave2d_last_error(void);
+
+/* Number of kernels the library has launched in this process (graph
+ * launches count every kernel node).  For launch accounting in benchmarks. */
+int64_t wave2d_launch_count(void);
+
+/* Stability limit of a scheme (conventional = 1 for the comparison scheme). */
+double wave2d_lambda_max(int scheme, int conventional);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* WAVE2D_H */

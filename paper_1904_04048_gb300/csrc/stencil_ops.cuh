@@ -1,0 +1,133 @@
+// Per-node arithmetic of the explicit schemes of arXiv:1904.04048, Section 6.
+//
+// Every kernel of the library (one-node-per-thread, TMA tiles, temporal
+// blocking, batched) evaluates a node through the functions in this file, with
+// the operations pinned to round-to-nearest intrinsics so the compiler cannot
+// contract or reorder them differently from one kernel to the next.  The
+// results of different tilings are therefore bitwise identical.
+//
+// Stencil sums (Eq. notations2, read with i - q1 in the third term):
+//   delta(1,0) = ((e + w) + (n + s)) - 4c
+//   delta(1,1) = ((ne + sw) + (nw + se)) - 4c
+//   delta(2,0) = ((ee + ww) + (nn + ss)) - 4c
+// The pairing of opposite neighbours makes each sum invariant under the eight
+// symmetries of the square grid bit for bit (every rotation or reflection
+// only swaps operands of a commutative addition).
+#pragma once
+#include <cstdint>
+
+namespace w2d {
+
+// ----------------------------------------------------------------------------
+// Double-float ("FP32x2") value: an unevaluated sum hi + lo with
+// |lo| <= ulp(hi)/2.  Error-free transforms: TwoSum (Knuth), Fast2Sum
+// (Dekker 1971), TwoProd with a fused multiply-add.
+// ----------------------------------------------------------------------------
+struct df {
+    float hi, lo;
+};
+
+__device__ __forceinline__ df two_sum(float a, float b) {
+    float s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return {s, e};
+}
+__device__ __forceinline__ df fast_two_sum(float a, float b) {  // |a| >= |b|
+    float s = __fadd_rn(a, b);
+    float e = __fsub_rn(b, __fsub_rn(s, a));
+    return {s, e};
+}
+// Accurate double-float addition (both parts through TwoSum).
+__device__ __forceinline__ df df_add(df x, df y) {
+    df s = two_sum(x.hi, y.hi);
+    df t = two_sum(x.lo, y.lo);
+    float e = __fadd_rn(s.lo, t.hi);
+    df u = fast_two_sum(s.hi, e);
+    float f = __fadd_rn(t.lo, u.lo);
+    return fast_two_sum(u.hi, f);
+}
+__device__ __forceinline__ df df_neg(df x) { return {-x.hi, -x.lo}; }
+// Product of two double-float numbers (the low-times-low term is dropped).
+__device__ __forceinline__ df df_mul(df a, df x) {
+    float p = __fmul_rn(a.hi, x.hi);
+    float e = __fmaf_rn(a.hi, x.hi, -p);
+    e = __fmaf_rn(a.hi, x.lo, e);
+    e = __fmaf_rn(a.lo, x.hi, e);
+    return fast_two_sum(p, e);
+}
+// Scaling by a power of two is exact.
+__device__ __forceinline__ df df_scale(df x, float s) { return {__fmul_rn(x.hi, s), __fmul_rn(x.lo, s)}; }
+
+// ----------------------------------------------------------------------------
+// Uniform operation set over float, double and df.
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ float vadd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double vadd(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ df vadd(df a, df b) { return df_add(a, b); }
+
+__device__ __forceinline__ float vscale(float a, float s) { return __fmul_rn(a, s); }
+__device__ __forceinline__ double vscale(double a, float s) { return __dmul_rn(a, (double)s); }
+__device__ __forceinline__ df vscale(df a, float s) { return df_scale(a, s); }
+
+// a * d + acc
+__device__ __forceinline__ float vfma(float a, float d, float acc) { return __fmaf_rn(a, d, acc); }
+__device__ __forceinline__ double vfma(double a, double d, double acc) { return __fma_rn(a, d, acc); }
+__device__ __forceinline__ df vfma(df a, df d, df acc) { return df_add(df_mul(a, d), acc); }
+
+__device__ __forceinline__ float vmul(float a, float d) { return __fmul_rn(a, d); }
+__device__ __forceinline__ double vmul(double a, double d) { return __dmul_rn(a, d); }
+__device__ __forceinline__ df vmul(df a, df d) { return df_mul(a, d); }
+
+__device__ __forceinline__ float vsub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double vsub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ df vsub(df a, df b) { return df_add(a, df_neg(b)); }
+
+template <typename V>
+struct Coef3 {
+    V a10, a11, a20;
+};
+
+// Values of one level around a node.  n/s are rows j+1 / j-1, e/w columns
+// i+1 / i-1; the second ring (ee, ww, nn, ss) is used by the 13-point scheme.
+template <typename V>
+struct Nbr {
+    V c, e, w, n, s, ne, nw, se, sw, ee, ww, nn, ss;
+};
+
+template <int S, typename V>
+__device__ __forceinline__ V lambda_sum(const Nbr<V>& u, const Coef3<V>& a) {
+    V m4c = vscale(u.c, -4.0f);
+    V d10 = vadd(vadd(vadd(u.e, u.w), vadd(u.n, u.s)), m4c);
+    V L = vmul(a.a10, d10);
+    if constexpr (S >= 9) {
+        V d11 = vadd(vadd(vadd(u.ne, u.sw), vadd(u.nw, u.se)), m4c);
+        L = vfma(a.a11, d11, L);
+    }
+    if constexpr (S == 13) {
+        V d20 = vadd(vadd(vadd(u.ee, u.ww), vadd(u.nn, u.ss)), m4c);
+        L = vfma(a.a20, d20, L);
+    }
+    return L;
+}
+
+// Two-step (Eq. A2): u^{k+1} = (2 u^k - u^{k-1}) + Lambda_a(u^k).
+template <int S, typename V>
+__device__ __forceinline__ V two_step_update(const Nbr<V>& u, V prev, const Coef3<V>& a) {
+    V L = lambda_sum<S>(u, a);
+    V base = vsub(vscale(u.c, 2.0f), prev);
+    return vadd(base, L);
+}
+
+// First step (Eq. A1), always in FP64:
+// u^1 = (u^0 + tau v^0) + (Lambda_{a/2}(u^0) + tau Lambda_b(v^0)).
+template <int S>
+__device__ __forceinline__ double first_step_update(const Nbr<double>& u, const Nbr<double>& v,
+                                                    const Coef3<double>& ahalf,
+                                                    const Coef3<double>& b, double tau) {
+    double Lu = lambda_sum<S>(u, ahalf);
+    double Lv = lambda_sum<S>(v, b);
+    return __dadd_rn(__fma_rn(tau, v.c, u.c), __fma_rn(tau, Lv, Lu));
+}
+
+}  // namespace w2d

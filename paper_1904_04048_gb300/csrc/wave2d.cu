@@ -1,0 +1,867 @@
+// C-ABI implementation of include/wave2d.h: handles, memory, dispatch.
+//
+// The paper's method (arXiv:1904.04048, Sections 3 and 6) runs entirely in the
+// kernels of kernels.cuh; this file validates arguments, lays out device
+// memory, builds the coefficient tables of Section 6 and the TMA descriptors,
+// and launches the kernels on the handle's stream.
+#include <cudaTypedefs.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "wave2d_impl.cuh"
+
+namespace w2d {
+
+// ------------------------------------------------------------------ errors
+static thread_local std::string t_err;
+
+int set_error(int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    t_err = buf;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+    return set_error(e == cudaErrorMemoryAllocation ? WAVE2D_ERR_OOM : WAVE2D_ERR_CUDA, "%s: %s (%s)",
+                     what, cudaGetErrorString(e), cudaGetErrorName(e));
+}
+
+#define W2D_CUDA(call, what)                      \
+    do {                                          \
+        cudaError_t e_ = (call);                  \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+#define W2D_LAUNCHED(what)                                   \
+    do {                                                     \
+        cudaError_t e_ = cudaGetLastError();                 \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what);   \
+        g_launches.fetch_add(1, std::memory_order_relaxed);  \
+    } while (0)
+
+std::atomic<int64_t> g_launches{0};
+
+// -------------------------------------------------------------- allocation
+static std::mutex g_alloc_mu;
+static Allocator g_alloc;
+
+Allocator current_allocator() {
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    return g_alloc;
+}
+
+void* dev_alloc(const Allocator& a, size_t bytes, cudaStream_t s) {
+    if (bytes == 0) bytes = 256;
+    if (a.alloc) return a.alloc(bytes, (void*)s, a.ctx);
+    void* p = nullptr;
+    if (cudaMallocAsync(&p, bytes, s) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+
+void dev_free(const Allocator& a, void* p, size_t bytes, cudaStream_t s) {
+    if (!p) return;
+    if (a.release) {
+        a.release(p, bytes, (void*)s, a.ctx);
+        return;
+    }
+    cudaFreeAsync(p, s);
+}
+
+// ------------------------------------------------------------ coefficients
+// Section 6: Eq. comp5.1/5.2, comp9.1/9.2, comp13.1/13.2 written as
+// Lambda_a / Lambda_b coefficients; conventional comparison schemes: b = 0
+// and, for nine points, the isotropic Laplacian of Eq. comp9.2b.
+static void scheme_coefficients(int scheme, bool conventional, double lam, double a[3], double b[3]) {
+    const double l2 = lam * lam, l4 = l2 * l2;
+    a[0] = a[1] = a[2] = b[0] = b[1] = b[2] = 0.0;
+    switch (scheme) {
+        case 5:
+            a[0] = l2;
+            b[0] = l2 / 6.0;
+            break;
+        case 9:
+            if (conventional) {
+                a[0] = 2.0 * l2 / 3.0;
+                a[1] = l2 / 6.0;
+            } else {
+                a[0] = l2 * (1.0 - l2 / 3.0);
+                a[1] = l4 / 6.0;
+                b[0] = l2 / 6.0 * (1.0 - l2 / 5.0);
+                b[1] = l4 / 60.0;
+            }
+            break;
+        case 13:
+            a[0] = l2 * (4.0 - 2.0 * l2) / 3.0;
+            a[1] = l4 / 6.0;
+            a[2] = l2 * (l2 - 1.0) / 12.0;
+            b[0] = l2 / 6.0 * (4.0 / 3.0 - 2.0 * l2 / 5.0);
+            b[1] = l4 / 60.0;
+            b[2] = l2 / 6.0 * (l2 / 20.0 - 1.0 / 12.0);
+            break;
+    }
+    if (conventional) b[0] = b[1] = b[2] = 0.0;
+}
+
+static double lambda_max_of(int scheme, bool conventional) {
+    switch (scheme) {
+        case 5:
+        case 13:
+            return 1.0 / std::sqrt(2.0);
+        case 9:
+            return conventional ? std::sqrt(3.0) / 2.0 : std::sqrt((3.0 - std::sqrt(3.0)) / 2.0);
+    }
+    return 0.0;
+}
+
+template <typename V>
+static Coef3<V> coef_as(const double a[3]);
+template <>
+Coef3<double> coef_as<double>(const double a[3]) { return {a[0], a[1], a[2]}; }
+template <>
+Coef3<float> coef_as<float>(const double a[3]) {
+    return {(float)a[0], (float)a[1], (float)a[2]};
+}
+static df split_df(double v) {
+    const float h = (float)v;
+    return {h, (float)(v - (double)h)};
+}
+template <>
+Coef3<df> coef_as<df>(const double a[3]) { return {split_df(a[0]), split_df(a[1]), split_df(a[2])}; }
+
+// --------------------------------------------------------------- dispatch
+template <int V>
+using IC = std::integral_constant<int, V>;
+template <bool V>
+using BC_ = std::integral_constant<bool, V>;
+
+template <typename Fn>
+static void dispatch_s(int scheme, Fn&& fn) {
+    switch (scheme) {
+        case 5: fn(IC<5>{}); break;
+        case 9: fn(IC<9>{}); break;
+        default: fn(IC<13>{}); break;
+    }
+}
+template <typename Fn>
+static void dispatch_dt(int dt, Fn&& fn) {
+    switch (dt) {
+        case DT_F64: fn(IC<DT_F64>{}); break;
+        case DT_F32: fn(IC<DT_F32>{}); break;
+        default: fn(IC<DT_F32X2>{}); break;
+    }
+}
+template <typename Fn>
+static void dispatch_bool(bool v, Fn&& fn) {
+    if (v) fn(BC_<true>{});
+    else fn(BC_<false>{});
+}
+
+// ----------------------------------------------------------- TMA encoding
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+        else
+            cudaGetLastError();
+    });
+    return fn;
+}
+
+static int encode_plane(CUtensorMap* tm, void* plane, const wave2d* h, int box_w, int box_h) {
+    auto enc = tensor_map_encoder();
+    if (!enc) return set_error(WAVE2D_ERR_CUDA, "cuTensorMapEncodeTiled is unavailable");
+    const cuuint64_t dims[2] = {(cuuint64_t)h->pitch, (cuuint64_t)h->rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)h->pitch * h->elem};
+    const cuuint32_t box[2] = {(cuuint32_t)box_w, (cuuint32_t)box_h};
+    const cuuint32_t estr[2] = {1, 1};
+    CUresult r = enc(tm, h->elem == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+                     plane, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                     CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return set_error(WAVE2D_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return WAVE2D_OK;
+}
+
+// Tile configurations of the TMA kernel (rows per tile, warps, stages).
+constexpr int kTmaNW = 8;
+constexpr int kTmaStages = 3;
+
+template <typename T, int S, int TH>
+static int tma_box(int& bw, int& bh, int& tw) {
+    using C = TmaCfg<T, S, TH, kTmaNW>;
+    bw = C::BOX_W;
+    bh = C::BOX_H;
+    tw = C::TW;
+    return C::STAGE_BYTES;
+}
+
+static int prepare_tma(wave2d* h) {
+    if (h->dtype == DT_F32X2) return set_error(WAVE2D_ERR_ARG, "TMA kernel supports F32 and F64 storage");
+    int bw = 0, bh = 0, tw = 0;
+    int rc = WAVE2D_OK;
+    dispatch_s(h->scheme, [&](auto Sc) {
+        constexpr int S = decltype(Sc)::value;
+        if (h->dtype == DT_F32) tma_box<float, S, 32>(bw, bh, tw);
+        else tma_box<double, S, 32>(bw, bh, tw);
+    });
+    for (int p = 0; p < 2 && rc == WAVE2D_OK; ++p) {
+        rc = encode_plane(&h->tm_cur[p], h->hi[p], h, bw, bh);
+        if (rc == WAVE2D_OK) rc = encode_plane(&h->tm_prev[p], h->hi[p], h, tw, 32);
+    }
+    h->tma_ready = (rc == WAVE2D_OK);
+    return rc;
+}
+
+// ------------------------------------------------------------ exact tables
+// u_e(i, j) = w0 (P_i Q_j - R_i S_j) + w1 (R_i Q_j + P_i S_j); see kernels.cuh.
+static void exact_tables(const wave2d* h, const wave2d_exact& ex, std::vector<double>& tab) {
+    tab.assign(2 * (size_t)h->nx + 2 * (size_t)h->ny, 0.0);
+    double* P = tab.data();
+    double* R = P + h->nx;
+    double* Q = R + h->nx;
+    double* S = Q + h->ny;
+    const double pi = 3.14159265358979323846;
+    for (int i = 0; i < h->nx; ++i) {
+        const double x = (i + ex.x_off) * h->h;
+        if (ex.kind == WAVE2D_EXACT_STANDING) P[i] = std::sin(2.0 * pi * ex.m * x);
+        else if (ex.kind == WAVE2D_EXACT_PLANE) {
+            P[i] = std::cos(ex.k1 * x);
+            R[i] = std::sin(ex.k1 * x);
+        }
+    }
+    for (int j = 0; j < h->ny; ++j) {
+        const double y = (j + ex.x_off) * h->h;
+        if (ex.kind == WAVE2D_EXACT_STANDING) Q[j] = std::sin(2.0 * pi * ex.m * y);
+        else if (ex.kind == WAVE2D_EXACT_PLANE) {
+            Q[j] = std::cos(ex.k2 * y);
+            S[j] = std::sin(ex.k2 * y);
+        }
+    }
+}
+
+static void exact_weights(const wave2d* h, const wave2d_exact& ex, double t, double& w0, double& w1) {
+    const double pi = 3.14159265358979323846;
+    w0 = w1 = 0.0;
+    if (ex.kind == WAVE2D_EXACT_STANDING) {
+        w0 = ex.amp * std::sin(2.0 * std::sqrt(2.0) * pi * ex.m * h->c * t);
+    } else if (ex.kind == WAVE2D_EXACT_PLANE) {
+        const double w = h->c * std::sqrt(ex.k1 * ex.k1 + ex.k2 * ex.k2);
+        w0 = ex.amp * std::cos(w * t);
+        w1 = ex.amp * std::sin(w * t);
+    }
+}
+
+static ExactTab make_tab(const wave2d* h, const double* dev_tab, const wave2d_exact& ex, double t) {
+    ExactTab et{};
+    et.kind = ex.kind;
+    et.P = dev_tab;
+    et.R = dev_tab + h->nx;
+    et.Q = dev_tab + 2 * (size_t)h->nx;
+    et.S = dev_tab + 2 * (size_t)h->nx + h->ny;
+    exact_weights(h, ex, t, et.w0, et.w1);
+    return et;
+}
+
+static Reduce make_reduce(const wave2d* h, double* acc, int accumulate) {
+    return Reduce{h->partials, h->counter, acc, h->status, accumulate};
+}
+
+// ------------------------------------------------------------ launches
+static dim3 grid2d(const wave2d* h) { return dim3((h->nx + 31) / 32, (h->ny + 7) / 8); }
+
+static int launch_first_step(wave2d* h, const double* du0, const double* dv0) {
+    double ahalf[3] = {h->a[0] / 2, h->a[1] / 2, h->a[2] / 2};
+    const Coef3<double> ca = coef_as<double>(ahalf), cb = coef_as<double>(h->b);
+    const ExactTab ex = make_tab(h, h->tab_track, h->track_ex, h->tau);
+    const Reduce rd = make_reduce(h, h->acc_track, 1);
+    const Level L0 = h->level(1), L1 = h->level(0);  // u^0 -> plane 1 (u^{k-1}), u^1 -> plane 0
+    dispatch_dt(h->dtype, [&](auto DTc) {
+        dispatch_s(h->scheme, [&](auto Sc) {
+            dispatch_bool(h->bc == WAVE2D_BC_PERIODIC, [&](auto Pc) {
+                dispatch_bool(h->tracking, [&](auto Tc) {
+                    k1_first_step<decltype(DTc)::value, decltype(Sc)::value, decltype(Pc)::value,
+                                  decltype(Tc)::value><<<grid2d(h), dim3(32, 8), 0, h->stream>>>(
+                        du0, dv0, L0, L1, h->geo(), ca, cb, h->tau, ex, rd);
+                });
+            });
+        });
+    });
+    W2D_LAUNCHED("first-step kernel launch");
+    return WAVE2D_OK;
+}
+
+static int launch_simple_step(wave2d* h, bool track) {
+    const Level cur = h->level(h->cur), nxt = h->level(1 - h->cur);
+    const ExactTab ex = track ? make_tab(h, h->tab_track, h->track_ex, (double)(h->k + 1) * h->tau) : ExactTab{};
+    const Reduce rd = make_reduce(h, h->acc_track, 1);
+    dispatch_dt(h->dtype, [&](auto DTc) {
+        constexpr int DT = decltype(DTc)::value;
+        using V = typename St<DT>::V;
+        const Coef3<V> a = coef_as<V>(h->a);
+        dispatch_s(h->scheme, [&](auto Sc) {
+            dispatch_bool(h->bc == WAVE2D_BC_PERIODIC, [&](auto Pc) {
+                dispatch_bool(track, [&](auto Tc) {
+                    k2_simple<DT, decltype(Sc)::value, decltype(Pc)::value, decltype(Tc)::value>
+                        <<<grid2d(h), dim3(32, 8), 0, h->stream>>>(cur, nxt, h->geo(), a, ex, rd);
+                });
+            });
+        });
+    });
+    W2D_LAUNCHED("two-step kernel launch");
+    return WAVE2D_OK;
+}
+
+template <typename T, int S, bool PER>
+static int launch_tma_t(wave2d* h) {
+    constexpr int TH = 32;
+    using C = TmaCfg<T, S, TH, kTmaNW>;
+    auto kern = k2_tma<T, S, PER, TH, kTmaNW, kTmaStages>;
+    const int smem = 2048 + kTmaStages * C::STAGE_BYTES;
+    static thread_local int configured_smem = -1;  // per instantiation
+    if (configured_smem != smem) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(TMA kernel)");
+        configured_smem = smem;
+    }
+    static thread_local int occ = 0;
+    if (occ == 0) {
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kTmaNW * 32, smem);
+        if (e != cudaSuccess || occ < 1) occ = 1;
+    }
+    const int tiles_x = (h->nx + C::TW - 1) / C::TW;
+    const int tiles_y = (h->ny + TH - 1) / TH;
+    const int n_tiles = tiles_x * tiles_y;
+    const int grid = std::min(n_tiles, occ * h->num_sms);
+    kern<<<grid, kTmaNW * 32, smem, h->stream>>>(h->tm_cur[h->cur], h->tm_prev[1 - h->cur],
+                                                 reinterpret_cast<T*>(h->hi[1 - h->cur]), h->geo(),
+                                                 coef_as<T>(h->a), tiles_x, n_tiles, h->status);
+    W2D_LAUNCHED("TMA two-step kernel launch");
+    return WAVE2D_OK;
+}
+
+static int launch_tma_step(wave2d* h) {
+    int rc = WAVE2D_OK;
+    dispatch_s(h->scheme, [&](auto Sc) {
+        constexpr int S = decltype(Sc)::value;
+        dispatch_bool(h->bc == WAVE2D_BC_PERIODIC, [&](auto Pc) {
+            constexpr bool P = decltype(Pc)::value;
+            rc = (h->dtype == DT_F32) ? launch_tma_t<float, S, P>(h) : launch_tma_t<double, S, P>(h);
+        });
+    });
+    return rc;
+}
+
+static int launch_one_step(wave2d* h) {
+    int rc;
+    if (h->kernel == WAVE2D_KERNEL_TMA) rc = launch_tma_step(h);
+    else rc = launch_simple_step(h, false);
+    if (rc != WAVE2D_OK) return rc;
+    h->cur = 1 - h->cur;
+    h->k += 1;
+    return WAVE2D_OK;
+}
+
+static void drop_graphs(wave2d* h) {
+    for (auto& g : h->graph)
+        if (g) {
+            cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
+    h->graph_steps = 0;
+}
+
+static int select_kernel(wave2d* h) {
+    int want = h->tune.kernel;
+    if (want == WAVE2D_KERNEL_AUTO) {
+        want = (h->dtype != DT_F32X2 && (int64_t)h->nx * h->ny >= 65536) ? WAVE2D_KERNEL_TMA
+                                                                         : WAVE2D_KERNEL_SIMPLE;
+    }
+    if (want == WAVE2D_KERNEL_TEMPORAL) want = WAVE2D_KERNEL_TMA;  // not built yet: fall to one step
+    if (want == WAVE2D_KERNEL_TMA && h->dtype == DT_F32X2) want = WAVE2D_KERNEL_SIMPLE;
+    if (want == WAVE2D_KERNEL_TMA && !h->tma_ready) {
+        int rc = prepare_tma(h);
+        if (rc != WAVE2D_OK) return rc;
+    }
+    h->kernel = want;
+    drop_graphs(h);
+    return WAVE2D_OK;
+}
+
+static bool want_graph(const wave2d* h, int64_t n) {
+    if (h->tune.use_graph == 0) return false;
+    if (h->tune.use_graph > 0) return n >= 2;
+    return n >= 64 && (int64_t)h->nx * h->ny <= (1 << 22);
+}
+
+constexpr int kGraphSteps = 32;
+
+static int run_graph(wave2d* h, int64_t& n) {
+    if (!h->graph[h->cur]) {
+        const int cur0 = h->cur;
+        const int64_t k0 = h->k;
+        cudaGraph_t g = nullptr;
+        W2D_CUDA(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+        const int64_t before = g_launches.load();
+        int rc = WAVE2D_OK;
+        for (int s = 0; s < kGraphSteps && rc == WAVE2D_OK; ++s) rc = launch_one_step(h);
+        cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+        g_launches.store(before);  // captured launches run only when the graph does
+        h->cur = cur0;
+        h->k = k0;
+        if (rc != WAVE2D_OK) {
+            if (g) cudaGraphDestroy(g);
+            return rc;
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "end capture");
+        e = cudaGraphInstantiate(&h->graph[cur0], g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return cuda_fail(e, "graph instantiate");
+        h->graph_steps = kGraphSteps;
+    }
+    while (n >= kGraphSteps) {
+        W2D_CUDA(cudaGraphLaunch(h->graph[h->cur], h->stream), "graph launch");
+        g_launches.fetch_add(kGraphSteps);
+        h->k += kGraphSteps;  // even count: parity unchanged
+        n -= kGraphSteps;
+    }
+    return WAVE2D_OK;
+}
+
+static bool valid_exact(const wave2d_exact* ex) {
+    return ex && (ex->kind == WAVE2D_EXACT_NONE || ex->kind == WAVE2D_EXACT_STANDING ||
+                  ex->kind == WAVE2D_EXACT_PLANE) &&
+           std::isfinite(ex->amp) && std::isfinite(ex->m) && std::isfinite(ex->k1) &&
+           std::isfinite(ex->k2) && std::isfinite(ex->x_off);
+}
+
+static int check_status(wave2d* h) {
+    int st = 0;
+    W2D_CUDA(cudaMemcpyAsync(&st, h->status, sizeof(int), cudaMemcpyDeviceToHost, h->stream), "status copy");
+    W2D_CUDA(cudaStreamSynchronize(h->stream), "stream synchronize");
+    if (st & STATUS_TIMEOUT) {
+        cudaMemsetAsync(h->status, 0, sizeof(int), h->stream);
+        return set_error(WAVE2D_ERR_TIMEOUT, "a device-side wait exceeded its limit");
+    }
+    return WAVE2D_OK;
+}
+
+}  // namespace w2d
+
+using namespace w2d;
+
+// ======================================================================
+// C ABI
+// ======================================================================
+extern "C" {
+
+const char* wave2d_last_error(void) { return t_err.c_str(); }
+
+int64_t wave2d_launch_count(void) { return g_launches.load(); }
+
+double wave2d_lambda_max(int scheme, int conventional) { return lambda_max_of(scheme, conventional != 0); }
+
+int wave2d_set_allocator(wave2d_alloc_fn alloc, wave2d_free_fn release, void* ctx) {
+    if ((alloc == nullptr) != (release == nullptr))
+        return set_error(WAVE2D_ERR_ARG, "allocator hook needs both alloc and free (or neither)");
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    g_alloc.alloc = alloc;
+    g_alloc.release = release;
+    g_alloc.ctx = alloc ? ctx : nullptr;
+    return WAVE2D_OK;
+}
+
+static void release_handle(wave2d* h) {
+    if (!h) return;
+    drop_graphs(h);
+    if (h->base) {
+        dev_free(h->alloc, h->base, h->base_bytes, h->stream);
+        cudaStreamSynchronize(h->stream);
+    }
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+    delete h;
+}
+
+int wave2d_create(const wave2d_grid* grid, double hh, double tau, double c, int scheme, wave2d_t* out) {
+    if (!grid || !out) return set_error(WAVE2D_ERR_ARG, "null argument");
+    *out = nullptr;
+    if (scheme != 5 && scheme != 9 && scheme != 13)
+        return set_error(WAVE2D_ERR_ARG, "scheme must be 5, 9 or 13 (got %d)", scheme);
+    if (grid->nx < 1 || grid->ny < 1 || grid->nx > 65536 || grid->ny > 65536)
+        return set_error(WAVE2D_ERR_ARG, "grid size %d x %d outside 1..65536", grid->nx, grid->ny);
+    if (grid->bc != WAVE2D_BC_ZERO && grid->bc != WAVE2D_BC_PERIODIC)
+        return set_error(WAVE2D_ERR_ARG, "unknown boundary condition %d", grid->bc);
+    if (grid->dtype != WAVE2D_F64 && grid->dtype != WAVE2D_F32 && grid->dtype != WAVE2D_F32X2)
+        return set_error(WAVE2D_ERR_ARG, "unknown dtype %d", grid->dtype);
+    if (grid->flags & ~(WAVE2D_ALLOW_UNSTABLE | WAVE2D_CONVENTIONAL))
+        return set_error(WAVE2D_ERR_ARG, "unknown flags 0x%x", grid->flags);
+    if (!(hh > 0) || !(tau > 0) || !(c > 0) || !std::isfinite(hh) || !std::isfinite(tau) || !std::isfinite(c))
+        return set_error(WAVE2D_ERR_ARG, "h, tau and c must be positive and finite");
+    const bool conventional = (grid->flags & WAVE2D_CONVENTIONAL) != 0;
+    const double lam = c * tau / hh;
+    const double lmax = lambda_max_of(scheme, conventional);
+    if (lam > lmax * (1.0 + 1e-12) && !(grid->flags & WAVE2D_ALLOW_UNSTABLE))
+        return set_error(WAVE2D_ERR_UNSTABLE, "Courant number %.17g exceeds the stability limit %.17g of the %d-point scheme",
+                         lam, lmax, scheme);
+
+    wave2d* h = new (std::nothrow) wave2d();
+    if (!h) return set_error(WAVE2D_ERR_OOM, "host allocation failed");
+    h->nx = grid->nx;
+    h->ny = grid->ny;
+    h->bc = grid->bc;
+    h->dtype = grid->dtype;
+    h->flags = grid->flags;
+    h->scheme = scheme;
+    h->R = scheme == 13 ? 2 : 1;
+    h->h = hh;
+    h->tau = tau;
+    h->c = c;
+    h->lam = lam;
+    h->lam_max = lmax;
+    scheme_coefficients(scheme, conventional, lam, h->a, h->b);
+    h->alloc = current_allocator();
+
+    cudaError_t e = cudaGetDevice(&h->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
+    if (e != cudaSuccess) {
+        delete h;
+        return cuda_fail(e, "no usable CUDA device");
+    }
+    h->stream = (cudaStream_t)grid->stream;
+    if (!h->stream) {
+        e = cudaStreamCreate(&h->stream);
+        if (e != cudaSuccess) {
+            delete h;
+            return cuda_fail(e, "stream create");
+        }
+        h->own_stream = true;
+    }
+
+    // Layout: level planes (2, or 4 for hi/lo), then scratch.
+    h->elem = (h->dtype == WAVE2D_F64) ? 8 : 4;
+    h->G = kGhost;
+    h->pitch = (int)round_up((size_t)h->nx + 2 * kGhost, 32);
+    h->rows = h->ny + 2 * kGhost;
+    h->plane_bytes = round_up((size_t)h->pitch * h->rows * h->elem, 1024);
+    const int nplanes = (h->dtype == WAVE2D_F32X2) ? 4 : 2;
+    const size_t k2_blocks = (size_t)((h->nx + 31) / 32) * ((h->ny + 7) / 8);
+    h->partial_blocks = std::max<size_t>(k2_blocks, 64 * 1024);
+    const size_t tab_doubles = 2 * (size_t)h->nx + 2 * (size_t)h->ny;
+    const size_t scratch = round_up(h->partial_blocks * 4 * sizeof(double), 256) + 256 /*counter*/ +
+                           256 /*acc_eval*/ + 256 /*acc_track*/ + 256 /*status*/ +
+                           2 * round_up(tab_doubles * sizeof(double), 256);
+    h->base_bytes = nplanes * h->plane_bytes + scratch;
+    h->base = dev_alloc(h->alloc, h->base_bytes, h->stream);
+    if (!h->base) {
+        release_handle(h);
+        return set_error(WAVE2D_ERR_OOM, "device allocation of %zu bytes failed", h->base_bytes);
+    }
+    char* p = (char*)h->base;
+    for (int q = 0; q < 2; ++q) h->hi[q] = p + q * h->plane_bytes;
+    if (nplanes == 4)
+        for (int q = 0; q < 2; ++q) h->lo[q] = p + (2 + q) * h->plane_bytes;
+    p += nplanes * h->plane_bytes;
+    h->partials = (double*)p;
+    p += round_up(h->partial_blocks * 4 * sizeof(double), 256);
+    h->counter = (unsigned*)p;
+    p += 256;
+    h->acc_eval = (double*)p;
+    p += 256;
+    h->acc_track = (double*)p;
+    p += 256;
+    h->status = (int*)p;
+    p += 256;
+    h->tab_eval = (double*)p;
+    p += round_up(tab_doubles * sizeof(double), 256);
+    h->tab_track = (double*)p;
+    e = cudaMemsetAsync(h->base, 0, h->base_bytes, h->stream);
+    if (e != cudaSuccess) {
+        int rc = cuda_fail(e, "memset");
+        release_handle(h);
+        return rc;
+    }
+    int rc = select_kernel(h);
+    if (rc != WAVE2D_OK) {
+        release_handle(h);
+        return rc;
+    }
+    *out = h;
+    return WAVE2D_OK;
+}
+
+void wave2d_destroy(wave2d_t h) { release_handle(h); }
+
+int wave2d_set_tuning(wave2d_t h, const wave2d_tune* tune) {
+    if (!h || !tune) return set_error(WAVE2D_ERR_ARG, "null argument");
+    if (tune->kernel < 0 || tune->kernel > WAVE2D_KERNEL_TEMPORAL)
+        return set_error(WAVE2D_ERR_ARG, "unknown kernel %d", tune->kernel);
+    if (tune->kernel == WAVE2D_KERNEL_TMA && h->dtype == WAVE2D_F32X2)
+        return set_error(WAVE2D_ERR_ARG, "the TMA kernel supports F32 and F64 storage only");
+    h->tune = *tune;
+    return select_kernel(h);
+}
+
+int wave2d_get_info(wave2d_t h, wave2d_info_t* info) {
+    if (!h || !info) return set_error(WAVE2D_ERR_ARG, "null argument");
+    std::memset(info, 0, sizeof *info);
+    info->lambda = h->lam;
+    info->h = h->h;
+    info->tau = h->tau;
+    info->c = h->c;
+    for (int q = 0; q < 3; ++q) {
+        info->a[q] = h->a[q];
+        info->b[q] = h->b[q];
+    }
+    info->lambda_max = h->lam_max;
+    info->k = h->k;
+    info->scheme = h->scheme;
+    info->radius = h->R;
+    info->dtype = h->dtype;
+    info->bc = h->bc;
+    info->nx = h->nx;
+    info->ny = h->ny;
+    info->pitch = h->pitch;
+    info->ghost = h->G;
+    info->device_bytes = (int64_t)h->base_bytes;
+    info->kernel = h->kernel;
+    info->temporal_t = 1;
+    return WAVE2D_OK;
+}
+
+int wave2d_track_error(wave2d_t h, const wave2d_exact* ex) {
+    if (!h) return set_error(WAVE2D_ERR_ARG, "null handle");
+    if (!ex) {
+        h->tracking = false;
+        return WAVE2D_OK;
+    }
+    if (!valid_exact(ex)) return set_error(WAVE2D_ERR_ARG, "invalid exact-solution description");
+    h->track_ex = *ex;
+    std::vector<double> tab;
+    exact_tables(h, *ex, tab);
+    W2D_CUDA(cudaMemcpyAsync(h->tab_track, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice,
+                             h->stream),
+             "exact table upload");
+    W2D_CUDA(cudaStreamSynchronize(h->stream), "stream synchronize");
+    h->tracking = true;
+    return WAVE2D_OK;
+}
+
+int wave2d_first_step(wave2d_t h, const double* u0, const double* v0, int on_device) {
+    if (!h || !u0 || !v0) return set_error(WAVE2D_ERR_ARG, "null argument");
+    const size_t n = (size_t)h->nx * h->ny;
+    const double* du0 = u0;
+    const double* dv0 = v0;
+    void* stage = nullptr;
+    if (!on_device) {
+        stage = dev_alloc(h->alloc, 2 * n * sizeof(double), h->stream);
+        if (!stage) return set_error(WAVE2D_ERR_OOM, "staging allocation failed");
+        W2D_CUDA(cudaMemcpyAsync(stage, u0, n * sizeof(double), cudaMemcpyHostToDevice, h->stream), "u0 upload");
+        W2D_CUDA(cudaMemcpyAsync((double*)stage + n, v0, n * sizeof(double), cudaMemcpyHostToDevice, h->stream),
+                 "v0 upload");
+        du0 = (const double*)stage;
+        dv0 = (const double*)stage + n;
+    }
+    W2D_CUDA(cudaMemsetAsync(h->acc_track, 0, 4 * sizeof(double), h->stream), "reset accumulators");
+    int rc = launch_first_step(h, du0, dv0);
+    if (stage) dev_free(h->alloc, stage, 2 * n * sizeof(double), h->stream);
+    if (rc != WAVE2D_OK) return rc;
+    h->cur = 0;  // plane 0 holds u^1, plane 1 holds u^0
+    h->k = 1;
+    h->initialized = true;
+    return WAVE2D_OK;
+}
+
+int wave2d_step_n(wave2d_t h, int64_t n) {
+    if (!h) return set_error(WAVE2D_ERR_ARG, "null handle");
+    if (n < 0) return set_error(WAVE2D_ERR_ARG, "negative step count");
+    if (!h->initialized) return set_error(WAVE2D_ERR_STATE, "step_n before first_step or set_state");
+    if (h->tracking) {
+        for (int64_t s = 0; s < n; ++s) {
+            int rc = launch_simple_step(h, true);
+            if (rc != WAVE2D_OK) return rc;
+            h->cur = 1 - h->cur;
+            h->k += 1;
+        }
+        return WAVE2D_OK;
+    }
+    if (want_graph(h, n)) {
+        int rc = run_graph(h, n);
+        if (rc != WAVE2D_OK) return rc;
+    }
+    for (int64_t s = 0; s < n; ++s) {
+        int rc = launch_one_step(h);
+        if (rc != WAVE2D_OK) return rc;
+    }
+    return WAVE2D_OK;
+}
+
+int wave2d_error_vs_exact(wave2d_t h, const wave2d_exact* ex, double* rel_l2, double* rel_linf,
+                          double* spacetime_E) {
+    if (!h) return set_error(WAVE2D_ERR_ARG, "null handle");
+    if (!h->initialized) return set_error(WAVE2D_ERR_STATE, "no time level computed yet");
+    wave2d_exact none{};
+    if (!ex) ex = &none;
+    if (!valid_exact(ex)) return set_error(WAVE2D_ERR_ARG, "invalid exact-solution description");
+    std::vector<double> tab;
+    if (ex->kind != WAVE2D_EXACT_NONE) {
+        exact_tables(h, *ex, tab);
+        W2D_CUDA(cudaMemcpyAsync(h->tab_eval, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice,
+                                 h->stream),
+                 "exact table upload");
+    }
+    const ExactTab et = make_tab(h, h->tab_eval, *ex, (double)h->k * h->tau);
+    const Reduce rd = make_reduce(h, h->acc_eval, 0);
+    const dim3 grd(std::min((h->nx + 255) / 256, 64), std::min(h->ny, 1024));
+    dispatch_dt(h->dtype, [&](auto DTc) {
+        k4_norms<decltype(DTc)::value><<<grd, 256, 0, h->stream>>>(h->level(h->cur), h->geo(), et, rd);
+    });
+    W2D_LAUNCHED("norm kernel launch");
+    double acc[4], accT[4];
+    int st = 0;
+    W2D_CUDA(cudaMemcpyAsync(acc, h->acc_eval, sizeof acc, cudaMemcpyDeviceToHost, h->stream), "norm copy");
+    W2D_CUDA(cudaMemcpyAsync(accT, h->acc_track, sizeof accT, cudaMemcpyDeviceToHost, h->stream), "norm copy");
+    W2D_CUDA(cudaMemcpyAsync(&st, h->status, sizeof st, cudaMemcpyDeviceToHost, h->stream), "status copy");
+    W2D_CUDA(cudaStreamSynchronize(h->stream), "stream synchronize");
+    if (ex->kind == WAVE2D_EXACT_NONE) {
+        if (rel_l2) *rel_l2 = std::sqrt(acc[0]);
+        if (rel_linf) *rel_linf = acc[2];
+    } else {
+        if (rel_l2) *rel_l2 = std::sqrt(acc[0] / acc[1]);
+        if (rel_linf) *rel_linf = acc[2] / acc[3];
+    }
+    if (spacetime_E) *spacetime_E = h->tracking ? std::sqrt(accT[0] / accT[1]) : NAN;
+    if (st) cudaMemsetAsync(h->status, 0, sizeof(int), h->stream);
+    if (st & STATUS_TIMEOUT) return set_error(WAVE2D_ERR_TIMEOUT, "a device-side wait exceeded its limit");
+    if (st & STATUS_NONFINITE) return set_error(WAVE2D_ERR_NONFINITE, "the field contains NaN or Inf");
+    return WAVE2D_OK;
+}
+
+int wave2d_get_state(wave2d_t h, double* u_prev, double* u_cur, int64_t* k) {
+    if (!h) return set_error(WAVE2D_ERR_ARG, "null handle");
+    if (!h->initialized) return set_error(WAVE2D_ERR_STATE, "no state yet");
+    const size_t n = (size_t)h->nx * h->ny;
+    double* stage = (double*)dev_alloc(h->alloc, 2 * n * sizeof(double), h->stream);
+    if (!stage) return set_error(WAVE2D_ERR_OOM, "staging allocation failed");
+    dispatch_dt(h->dtype, [&](auto DTc) {
+        constexpr int DT = decltype(DTc)::value;
+        k_pack<DT><<<grid2d(h), dim3(32, 8), 0, h->stream>>>(h->level(1 - h->cur), h->geo(), stage);
+        k_pack<DT><<<grid2d(h), dim3(32, 8), 0, h->stream>>>(h->level(h->cur), h->geo(), stage + n);
+    });
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess && u_prev)
+        e = cudaMemcpyAsync(u_prev, stage, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess && u_cur)
+        e = cudaMemcpyAsync(u_cur, stage + n, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+    dev_free(h->alloc, stage, 2 * n * sizeof(double), h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "get_state");
+    g_launches.fetch_add(2);
+    if (k) *k = h->k;
+    return check_status(h);
+}
+
+int wave2d_set_state(wave2d_t h, const double* u_prev, const double* u_cur, int64_t k, int on_device) {
+    if (!h || !u_prev || !u_cur) return set_error(WAVE2D_ERR_ARG, "null argument");
+    if (k < 1) return set_error(WAVE2D_ERR_ARG, "level index k must be >= 1");
+    const size_t n = (size_t)h->nx * h->ny;
+    const double* dp = u_prev;
+    const double* dc = u_cur;
+    double* stage = nullptr;
+    if (!on_device) {
+        stage = (double*)dev_alloc(h->alloc, 2 * n * sizeof(double), h->stream);
+        if (!stage) return set_error(WAVE2D_ERR_OOM, "staging allocation failed");
+        W2D_CUDA(cudaMemcpyAsync(stage, u_prev, n * sizeof(double), cudaMemcpyHostToDevice, h->stream), "upload");
+        W2D_CUDA(cudaMemcpyAsync(stage + n, u_cur, n * sizeof(double), cudaMemcpyHostToDevice, h->stream), "upload");
+        dp = stage;
+        dc = stage + n;
+    }
+    h->cur = 0;
+    dispatch_dt(h->dtype, [&](auto DTc) {
+        constexpr int DT = decltype(DTc)::value;
+        dispatch_bool(h->bc == WAVE2D_BC_PERIODIC, [&](auto Pc) {
+            k_unpack<DT, decltype(Pc)::value><<<grid2d(h), dim3(32, 8), 0, h->stream>>>(dp, h->level(1), h->geo());
+            k_unpack<DT, decltype(Pc)::value><<<grid2d(h), dim3(32, 8), 0, h->stream>>>(dc, h->level(0), h->geo());
+        });
+    });
+    cudaError_t e = cudaGetLastError();
+    if (stage) dev_free(h->alloc, stage, 2 * n * sizeof(double), h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "set_state");
+    g_launches.fetch_add(2);
+    h->k = k;
+    h->initialized = true;
+    drop_graphs(h);
+    return WAVE2D_OK;
+}
+
+int64_t wave2d_raw_bytes(wave2d_t h) {
+    if (!h) return set_error(WAVE2D_ERR_ARG, "null handle");
+    return (int64_t)((h->dtype == WAVE2D_F32X2 ? 4 : 2) * h->plane_bytes);
+}
+
+// Raw layout: [u^{k-1} hi][u^k hi] (+ [u^{k-1} lo][u^k lo] for F32X2), each
+// plane_bytes long, ghost ring included.
+int wave2d_get_raw(wave2d_t h, void* dst, int64_t bytes, int64_t* k) {
+    if (!h || !dst) return set_error(WAVE2D_ERR_ARG, "null argument");
+    if (!h->initialized) return set_error(WAVE2D_ERR_STATE, "no state yet");
+    if (bytes < wave2d_raw_bytes(h)) return set_error(WAVE2D_ERR_ARG, "buffer too small");
+    char* d = (char*)dst;
+    const int order[2] = {1 - h->cur, h->cur};
+    for (int q = 0; q < 2; ++q) {
+        W2D_CUDA(cudaMemcpyAsync(d + q * h->plane_bytes, h->hi[order[q]], h->plane_bytes, cudaMemcpyDeviceToHost,
+                                 h->stream),
+                 "raw copy");
+        if (h->lo[0])
+            W2D_CUDA(cudaMemcpyAsync(d + (2 + q) * h->plane_bytes, h->lo[order[q]], h->plane_bytes,
+                                     cudaMemcpyDeviceToHost, h->stream),
+                     "raw copy");
+    }
+    W2D_CUDA(cudaStreamSynchronize(h->stream), "stream synchronize");
+    if (k) *k = h->k;
+    return WAVE2D_OK;
+}
+
+int wave2d_set_raw(wave2d_t h, const void* src, int64_t bytes, int64_t k) {
+    if (!h || !src) return set_error(WAVE2D_ERR_ARG, "null argument");
+    if (k < 1) return set_error(WAVE2D_ERR_ARG, "level index k must be >= 1");
+    if (bytes < wave2d_raw_bytes(h)) return set_error(WAVE2D_ERR_ARG, "buffer too small");
+    const char* s = (const char*)src;
+    h->cur = 1;  // plane 0 <- u^{k-1}, plane 1 <- u^k
+    for (int q = 0; q < 2; ++q) {
+        W2D_CUDA(cudaMemcpyAsync(h->hi[q], s + q * h->plane_bytes, h->plane_bytes, cudaMemcpyHostToDevice, h->stream),
+                 "raw copy");
+        if (h->lo[0])
+            W2D_CUDA(cudaMemcpyAsync(h->lo[q], s + (2 + q) * h->plane_bytes, h->plane_bytes, cudaMemcpyHostToDevice,
+                                     h->stream),
+                     "raw copy");
+    }
+    W2D_CUDA(cudaStreamSynchronize(h->stream), "stream synchronize");
+    h->k = k;
+    h->initialized = true;
+    drop_graphs(h);
+    return WAVE2D_OK;
+}
+
+int wave2d_sync(wave2d_t h) {
+    if (!h) return set_error(WAVE2D_ERR_ARG, "null handle");
+    return check_status(h);
+}
+
+}  // extern "C"

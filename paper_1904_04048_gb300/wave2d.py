@@ -1,0 +1,277 @@
+"""ctypes binding of ``include/wave2d.h`` (argument marshalling only).
+
+Every step of the method runs in the CUDA library ``libwave2d.so``; this
+module converts arguments and raises on error codes.  There is no fallback:
+if the library is missing or cannot load, importing the binding fails.
+
+PyTorch is used for device memory (its caching allocator is installed as the
+library's allocation hook by ``use_torch_allocator``) and for streams.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libwave2d.so")
+
+OK = 0
+ERR_ARG, ERR_UNSTABLE, ERR_OOM, ERR_CUDA, ERR_NONFINITE, ERR_TIMEOUT, ERR_STATE = -1, -2, -3, -4, -5, -6, -7
+BC_ZERO, BC_PERIODIC = 0, 1
+F64, F32, F32X2 = 0, 1, 2
+ALLOW_UNSTABLE, CONVENTIONAL = 1, 2
+EXACT_NONE, EXACT_STANDING, EXACT_PLANE = 0, 1, 2
+KERNEL_AUTO, KERNEL_SIMPLE, KERNEL_TMA, KERNEL_TEMPORAL = 0, 1, 2, 3
+
+_NAMES = {ERR_ARG: "ERR_ARG", ERR_UNSTABLE: "ERR_UNSTABLE", ERR_OOM: "ERR_OOM", ERR_CUDA: "ERR_CUDA",
+          ERR_NONFINITE: "ERR_NONFINITE", ERR_TIMEOUT: "ERR_TIMEOUT", ERR_STATE: "ERR_STATE"}
+
+
+class Wave2DError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class wave2d_exact(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("reserved", ctypes.c_int32), ("amp", ctypes.c_double),
+                ("m", ctypes.c_double), ("k1", ctypes.c_double), ("k2", ctypes.c_double),
+                ("x_off", ctypes.c_double)]
+
+
+class wave2d_grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("bc", ctypes.c_int32),
+                ("dtype", ctypes.c_int32), ("flags", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("stream", ctypes.c_void_p)]
+
+
+class wave2d_tune(ctypes.Structure):
+    _fields_ = [("kernel", ctypes.c_int32), ("tile_h", ctypes.c_int32), ("temporal_t", ctypes.c_int32),
+                ("use_graph", ctypes.c_int32)]
+
+
+class wave2d_info_t(ctypes.Structure):
+    _fields_ = [("lambda_", ctypes.c_double), ("h", ctypes.c_double), ("tau", ctypes.c_double),
+                ("c", ctypes.c_double), ("a", ctypes.c_double * 3), ("b", ctypes.c_double * 3),
+                ("lambda_max", ctypes.c_double), ("k", ctypes.c_int64), ("scheme", ctypes.c_int32),
+                ("radius", ctypes.c_int32), ("dtype", ctypes.c_int32), ("bc", ctypes.c_int32),
+                ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("pitch", ctypes.c_int32),
+                ("ghost", ctypes.c_int32), ("device_bytes", ctypes.c_int64), ("kernel", ctypes.c_int32),
+                ("temporal_t", ctypes.c_int32)]
+
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+
+# Every exported symbol of include/wave2d.h with (restype, argtypes).
+_P = ctypes.c_void_p
+_D = ctypes.POINTER(ctypes.c_double)
+_I64P = ctypes.POINTER(ctypes.c_int64)
+SIGNATURES = {
+    "wave2d_set_allocator": (ctypes.c_int, [ALLOC_FN, FREE_FN, _P]),
+    "wave2d_create": (ctypes.c_int, [ctypes.POINTER(wave2d_grid), ctypes.c_double, ctypes.c_double,
+                                     ctypes.c_double, ctypes.c_int, ctypes.POINTER(_P)]),
+    "wave2d_first_step": (ctypes.c_int, [_P, _P, _P, ctypes.c_int]),
+    "wave2d_step_n": (ctypes.c_int, [_P, ctypes.c_int64]),
+    "wave2d_error_vs_exact": (ctypes.c_int, [_P, ctypes.POINTER(wave2d_exact), _D, _D, _D]),
+    "wave2d_track_error": (ctypes.c_int, [_P, ctypes.POINTER(wave2d_exact)]),
+    "wave2d_get_state": (ctypes.c_int, [_P, _P, _P, _I64P]),
+    "wave2d_set_state": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64, ctypes.c_int]),
+    "wave2d_raw_bytes": (ctypes.c_int64, [_P]),
+    "wave2d_get_raw": (ctypes.c_int, [_P, _P, ctypes.c_int64, _I64P]),
+    "wave2d_set_raw": (ctypes.c_int, [_P, _P, ctypes.c_int64, ctypes.c_int64]),
+    "wave2d_set_tuning": (ctypes.c_int, [_P, ctypes.POINTER(wave2d_tune)]),
+    "wave2d_get_info": (ctypes.c_int, [_P, ctypes.POINTER(wave2d_info_t)]),
+    "wave2d_sync": (ctypes.c_int, [_P]),
+    "wave2d_destroy": (None, [_P]),
+    "wave2d_last_error": (ctypes.c_char_p, []),
+    "wave2d_launch_count": (ctypes.c_int64, []),
+    "wave2d_lambda_max": (ctypes.c_double, [ctypes.c_int, ctypes.c_int]),
+}
+
+_lib = None
+
+
+def lib():
+    """Load libwave2d.so (raises if it is missing: there is no CPU path)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"wave2d CUDA library not built: {LIB_PATH} is missing "
+                              "(run paper_1904_04048_gb300.build.build())")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def last_error() -> str:
+    return lib().wave2d_last_error().decode()
+
+
+def check(rc: int) -> int:
+    if rc < 0:
+        raise Wave2DError(rc, last_error())
+    return rc
+
+
+def launch_count() -> int:
+    return lib().wave2d_launch_count()
+
+
+def lambda_max(scheme: int, conventional: bool = False) -> float:
+    return lib().wave2d_lambda_max(scheme, int(conventional))
+
+
+# ----------------------------------------------------------------- allocator
+_alloc_refs = None
+
+
+def use_torch_allocator():
+    """Route the library's device allocations through PyTorch's caching allocator."""
+    global _alloc_refs
+    import torch
+
+    def _alloc(nbytes, stream, ctx):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), torch.cuda.current_device(),
+                                                      int(stream or 0))
+        except Exception:  # out of memory: the library reports WAVE2D_ERR_OOM
+            return None
+
+    def _free(ptr, nbytes, stream, ctx):
+        torch.cuda.caching_allocator_delete(int(ptr))
+
+    refs = (ALLOC_FN(_alloc), FREE_FN(_free))
+    check(lib().wave2d_set_allocator(refs[0], refs[1], None))
+    _alloc_refs = refs
+
+
+def use_default_allocator():
+    global _alloc_refs
+    check(lib().wave2d_set_allocator(ALLOC_FN(), FREE_FN(), None))
+    _alloc_refs = None
+
+
+# ----------------------------------------------------------------- helpers
+def exact(kind=EXACT_NONE, amp=1.0, m=1.0, k1=0.0, k2=0.0, x_off=0.0) -> wave2d_exact:
+    return wave2d_exact(kind, 0, amp, m, k1, k2, x_off)
+
+
+def _host_f64(a, n):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if a.size != n:
+        raise ValueError(f"expected {n} values, got {a.size}")
+    return a
+
+
+def _ptr(a):
+    """(pointer, on_device) of a numpy array or CUDA torch tensor of float64."""
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data_as(ctypes.c_void_p), 0
+    import torch
+    if isinstance(a, torch.Tensor):
+        if a.dtype != torch.float64 or not a.is_contiguous():
+            raise ValueError("device inputs must be contiguous float64 tensors")
+        return ctypes.c_void_p(a.data_ptr()), int(a.is_cuda)
+    raise TypeError(type(a))
+
+
+class Wave2D:
+    """One simulation handle (``wave2d_t``)."""
+
+    def __init__(self, nx, ny, h, tau, c=1.0, scheme=13, bc=BC_ZERO, dtype=F32, flags=0, stream=None):
+        g = wave2d_grid(int(nx), int(ny), int(bc), int(dtype), int(flags), 0,
+                        ctypes.c_void_p(int(stream) if stream else 0))
+        out = ctypes.c_void_p()
+        check(lib().wave2d_create(ctypes.byref(g), float(h), float(tau), float(c), int(scheme),
+                                  ctypes.byref(out)))
+        self._h = out
+        self.nx, self.ny = int(nx), int(ny)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().wave2d_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def handle(self):
+        return self._h
+
+    def first_step(self, u0, v0):
+        n = self.nx * self.ny
+        if isinstance(u0, np.ndarray) or not hasattr(u0, "data_ptr"):
+            u0 = _host_f64(u0, n)
+            v0 = _host_f64(v0, n)
+        pu, du = _ptr(u0)
+        pv, dv = _ptr(v0)
+        if du != dv:
+            raise ValueError("u0 and v0 must both be on the host or both on the device")
+        check(lib().wave2d_first_step(self._h, pu, pv, du))
+
+    def step_n(self, n):
+        check(lib().wave2d_step_n(self._h, int(n)))
+
+    def error_vs_exact(self, ex: wave2d_exact | None = None):
+        l2, linf, E = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        rc = lib().wave2d_error_vs_exact(self._h, ctypes.byref(ex) if ex is not None else None,
+                                         ctypes.byref(l2), ctypes.byref(linf), ctypes.byref(E))
+        check(rc)
+        return l2.value, linf.value, E.value
+
+    def track_error(self, ex: wave2d_exact | None):
+        check(lib().wave2d_track_error(self._h, ctypes.byref(ex) if ex is not None else None))
+
+    def get_state(self):
+        up = np.empty((self.ny, self.nx))
+        uc = np.empty((self.ny, self.nx))
+        k = ctypes.c_int64()
+        check(lib().wave2d_get_state(self._h, up.ctypes.data_as(ctypes.c_void_p),
+                                     uc.ctypes.data_as(ctypes.c_void_p), ctypes.byref(k)))
+        return up, uc, k.value
+
+    def set_state(self, u_prev, u_cur, k):
+        n = self.nx * self.ny
+        up, uc = _host_f64(u_prev, n), _host_f64(u_cur, n)
+        check(lib().wave2d_set_state(self._h, up.ctypes.data_as(ctypes.c_void_p),
+                                     uc.ctypes.data_as(ctypes.c_void_p), int(k), 0))
+
+    def get_raw(self):
+        nb = check(lib().wave2d_raw_bytes(self._h))
+        buf = np.empty(nb, dtype=np.uint8)
+        k = ctypes.c_int64()
+        check(lib().wave2d_get_raw(self._h, buf.ctypes.data_as(ctypes.c_void_p), nb, ctypes.byref(k)))
+        return buf, k.value
+
+    def set_raw(self, buf, k):
+        buf = np.ascontiguousarray(buf, dtype=np.uint8)
+        check(lib().wave2d_set_raw(self._h, buf.ctypes.data_as(ctypes.c_void_p), buf.size, int(k)))
+
+    def set_tuning(self, kernel=KERNEL_AUTO, tile_h=0, temporal_t=0, use_graph=-1):
+        t = wave2d_tune(int(kernel), int(tile_h), int(temporal_t), int(use_graph))
+        check(lib().wave2d_set_tuning(self._h, ctypes.byref(t)))
+
+    def info(self) -> wave2d_info_t:
+        inf = wave2d_info_t()
+        check(lib().wave2d_get_info(self._h, ctypes.byref(inf)))
+        return inf
+
+    def sync(self):
+        check(lib().wave2d_sync(self._h))

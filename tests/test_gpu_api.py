@@ -1,0 +1,172 @@
+"""GPU behaviour of the C ABI: state and checkpoints, error codes, stability
+guard, non-finite detection, CUDA-graph path, symmetry, allocator hook."""
+import math
+
+import numpy as np
+import pytest
+
+from gpu_util import TOL, rel_errors, smooth_ic
+from initial_data import BC_PERIODIC, BC_ZERO, LAMBDA_MAX
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def w():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1904_04048_gb300 import build
+    build.build()
+    from paper_1904_04048_gb300 import wave2d
+    return wave2d
+
+
+def test_state_errors(w):
+    with w.Wave2D(16, 16, 0.1, 0.05, scheme=5) as sim:
+        with pytest.raises(w.Wave2DError) as e:
+            sim.step_n(3)
+        assert e.value.code == w.ERR_STATE
+        with pytest.raises(w.Wave2DError) as e:
+            sim.get_state()
+        assert e.value.code == w.ERR_STATE
+        sim.first_step(np.zeros((16, 16)), np.ones((16, 16)))
+        with pytest.raises(w.Wave2DError) as e:
+            sim.step_n(-1)
+        assert e.value.code == w.ERR_ARG
+        sim.step_n(0)
+        assert sim.info().k == 1
+
+
+@pytest.mark.parametrize("dtype", [0, 1, 2])
+def test_checkpoint_resume_is_bitwise(w, dtype):
+    n = 96
+    u0, v0, h = smooth_ic(n, n, BC_PERIODIC, seed=1)
+    lam = 0.6
+    with w.Wave2D(n, n, h, lam * h, scheme=13, bc=BC_PERIODIC, dtype=dtype) as a:
+        a.first_step(u0, v0)
+        a.step_n(30)
+        raw, k = a.get_raw()
+        a.step_n(50)
+        _, ref, _ = a.get_state()
+    with w.Wave2D(n, n, h, lam * h, scheme=13, bc=BC_PERIODIC, dtype=dtype) as b:
+        b.set_raw(raw, k)
+        b.step_n(50)
+        _, got, kk = b.get_state()
+    assert kk == 81 and np.array_equal(got, ref)
+
+
+@pytest.mark.parametrize("dtype", [0, 1])
+def test_set_state_resumes(w, orc, dtype):
+    n = 50
+    u0, v0, h = smooth_ic(n, n, BC_ZERO, seed=2)
+    lam = 0.5
+    rp, rc, _ = orc.run(9, u0, v0, lam, lam * h, 10, bc=BC_ZERO)
+    with w.Wave2D(n, n, h, lam * h, scheme=9, bc=BC_ZERO, dtype=dtype) as sim:
+        sim.set_state(rp, rc, 10)
+        sim.step_n(20)
+        _, got, k = sim.get_state()
+    _, ref = orc.continue_run(9, rp, rc, lam, 20, bc=BC_ZERO)
+    assert k == 30
+    l2, linf = rel_errors(got, ref)
+    assert l2 < TOL[dtype] and linf < TOL[dtype]
+
+
+def test_graph_path_is_bitwise_equal(w):
+    n = 200
+    u0, v0, h = smooth_ic(n, n, BC_PERIODIC, seed=4)
+    out = []
+    for use_graph in (0, 1):
+        with w.Wave2D(n, n, h, 0.6 * h, scheme=13, bc=BC_PERIODIC, dtype=1) as sim:
+            sim.set_tuning(kernel=w.KERNEL_TMA, use_graph=use_graph)
+            sim.first_step(u0, v0)
+            sim.step_n(101)  # 3 graph replays of 32 steps + 5 single launches
+            out.append(sim.get_state())
+    assert out[0][2] == out[1][2] == 102
+    assert np.array_equal(out[0][1], out[1][1]) and np.array_equal(out[0][0], out[1][0])
+
+
+@pytest.mark.parametrize("bc", [BC_ZERO, BC_PERIODIC])
+@pytest.mark.parametrize("kernel", [1, 2])
+def test_d4_symmetry_is_bitwise(w, bc, kernel):
+    """Each stencil sum pairs opposite neighbours, so rotating or reflecting
+    the data permutes operands of commutative additions only."""
+    n = 131
+    u0, v0, h = smooth_ic(n, n, bc, seed=9)
+    def run(a, b):
+        with w.Wave2D(n, n, h, 0.6 * h, scheme=13, bc=bc, dtype=1) as sim:
+            sim.set_tuning(kernel=kernel)
+            sim.first_step(a, b)
+            sim.step_n(60)
+            return sim.get_state()[1]
+    ref = run(u0, v0)
+    for op in (lambda a: np.rot90(a).copy(), lambda a: a.T.copy(), lambda a: a[::-1].copy()):
+        assert np.array_equal(run(op(u0), op(v0)), op(ref))
+
+
+def test_instability_and_nonfinite_detection(w):
+    n = 64
+    rng = np.random.default_rng(0)
+    u0 = rng.standard_normal((n, n))
+    v0 = rng.standard_normal((n, n))
+    h = 1.0 / n
+    lam = 1.5 * LAMBDA_MAX[13]
+    with pytest.raises(w.Wave2DError) as e:
+        w.Wave2D(n, n, h, lam * h, scheme=13)
+    assert e.value.code == w.ERR_UNSTABLE
+    with w.Wave2D(n, n, h, lam * h, scheme=13, bc=BC_PERIODIC, dtype=1, flags=w.ALLOW_UNSTABLE) as sim:
+        sim.first_step(u0, v0)
+        sim.step_n(20)
+        l2, linf, _ = sim.error_vs_exact()
+        assert np.isfinite(l2) and l2 > 1e3
+        sim.step_n(2000)
+        with pytest.raises(w.Wave2DError) as e:
+            sim.error_vs_exact()
+        assert e.value.code == w.ERR_NONFINITE
+
+
+def test_stability_edge_is_accepted(w):
+    for scheme in (5, 9, 13):
+        lm = w.lambda_max(scheme)
+        with w.Wave2D(8, 8, 1.0, lm, scheme=scheme):
+            pass
+
+
+def test_device_inputs_and_torch_allocator(w, orc):
+    import torch
+    n = 80
+    u0, v0, h = smooth_ic(n, n, BC_ZERO, seed=6)
+    w.use_torch_allocator()
+    try:
+        with w.Wave2D(n, n, h, 0.5 * h, scheme=5, dtype=0) as sim:
+            sim.first_step(torch.from_numpy(u0).cuda(), torch.from_numpy(v0).cuda())
+            sim.step_n(25)
+            _, got, _ = sim.get_state()
+    finally:
+        w.use_default_allocator()
+    _, ref, _ = orc.run(5, u0, v0, 0.5, 0.5 * h, 26)
+    l2, linf = rel_errors(got, ref)
+    assert l2 < 1e-12 and linf < 1e-12
+
+
+def test_user_stream(w):
+    import torch
+    s = torch.cuda.Stream()
+    n = 64
+    u0, v0, h = smooth_ic(n, n, BC_PERIODIC, seed=8)
+    with w.Wave2D(n, n, h, 0.5 * h, scheme=9, bc=BC_PERIODIC, stream=s.cuda_stream) as sim:
+        sim.first_step(u0, v0)
+        sim.step_n(10)
+        sim.sync()
+        assert sim.info().k == 11
+
+
+def test_launch_counter_counts_kernels(w):
+    n = 64
+    u0, v0, h = smooth_ic(n, n, BC_PERIODIC, seed=8)
+    with w.Wave2D(n, n, h, 0.5 * h, scheme=9, bc=BC_PERIODIC) as sim:
+        sim.set_tuning(kernel=w.KERNEL_SIMPLE, use_graph=0)
+        sim.first_step(u0, v0)
+        c0 = w.launch_count()
+        sim.step_n(17)
+        assert w.launch_count() - c0 == 17
