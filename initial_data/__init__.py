@@ -112,7 +112,7 @@ def pulses_and_noise(n: int, seed: int = 2019, n_pulses: int = 16, bc: int = BC_
     K1, K2 = np.meshgrid(kidx, kidx, indexing="xy")
     mask = np.hypot(K1, K2) < nyquist_fraction * (n / 2.0)
     noise = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
-    v0 = np.real(np.fft.ifft2(noise * mask))
+    v0 = np.ascontiguousarray(np.real(np.fft.ifft2(noise * mask)))
     v0 /= np.max(np.abs(v0))
     return u0, v0
 

@@ -123,9 +123,11 @@ def test_spacetime_error_matches_oracle(orc, w, scheme, n, n_t, conv, bc, dtype)
     _, rc, err = orc.run(scheme, u0, v0, lam, lam * h, n_t, bc=bc, conventional=conv,
                          exact=orc.EXACT_STANDING, exact_params=(1.0, 1.0), h=h, x_off=x_off)
     E_ref = orc.relative_spacetime_error(err)
-    assert abs(E - E_ref) <= 1e-9 * E_ref, (E, E_ref)
+    # E is a relative error of the field, so rounding differences of the
+    # field (bounded by the dtype tolerance relative to ||u||) bound |dE|.
+    assert abs(E - E_ref) <= TOL[dtype] + 1e-9 * E_ref, (E, E_ref)
     s = orc.error_sums(uc, h, x_off, orc.EXACT_STANDING, (1.0, 1.0), 1.0, n_t * lam * h)
-    assert abs(l2 - math.sqrt(s[0] / s[1])) <= 1e-9 * l2
+    assert abs(l2 - math.sqrt(s[0] / s[1])) <= 1e-9 * l2  # same field: reduction order only
 
 
 def test_plane_wave_error_norms(orc, w):
