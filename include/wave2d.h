@@ -209,6 +209,32 @@ int wave2d_sync(wave2d_t h);
 void wave2d_destroy(wave2d_t h);
 const char *wave2d_last_error(void);
 
+/* Allocation-free variant of the FP64 norms of wave2d_error_vs_exact, for
+ * callers that cannot allocate device memory: code whose GPU memory is owned
+ * and budgeted by another allocator (a serving process that hands its whole
+ * memory pool to a framework), and latency-critical loops where a cudaMalloc
+ * would synchronise the device.  The paper has no counterpart; it is a
+ * service of this library.
+ *   field   device array of nx*ny values (F32 or F64 per dtype), row j at
+ *           field + j*ld elements; owned by the caller, only read.
+ *   h, c, t grid spacing, wave speed and time of the exact solution; ex as
+ *           for wave2d_error_vs_exact (NULL = WAVE2D_EXACT_NONE).
+ *   rel_l2, rel_linf  host outputs with the meaning of wave2d_error_vs_exact.
+ *   stream  cudaStream_t to run on (NULL = default stream); the call
+ *           synchronises it before returning.
+ * No device memory is allocated: the scratch (partial sums, result slots,
+ * exact-solution tables) is one file-scope __device__ array of about 320 KiB
+ * that every GPU loading the library holds until the process exits.  Limits:
+ * 1 <= nx, ny <= 8192, else WAVE2D_ERR_ARG.  The first call on each device
+ * looks up the array's address (cudaGetSymbolAddress) and caches it: make
+ * that first call before any stream capture.  All calls share the array and
+ * it keeps the last call's contents (the call clears what must start at
+ * zero): calls that overlap on the GPU, from any thread or stream, race and
+ * must be serialised by the caller. */
+int wave2d_error_norms_noalloc(const void *field, int dtype, int nx, int ny, int64_t ld, double h,
+                               double c, double t, const wave2d_exact *ex, double *rel_l2,
+                               double *rel_linf, void *stream);
+
 /* Number of kernels the library has launched in this process (graph
  * launches count every kernel node).  For launch accounting in benchmarks. */
 int64_t wave2d_launch_count(void);

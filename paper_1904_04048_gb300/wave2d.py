@@ -89,6 +89,9 @@ SIGNATURES = {
     "wave2d_last_error": (ctypes.c_char_p, []),
     "wave2d_launch_count": (ctypes.c_int64, []),
     "wave2d_lambda_max": (ctypes.c_double, [ctypes.c_int, ctypes.c_int]),
+    "wave2d_error_norms_noalloc": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int64,
+                                                  ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                                  ctypes.POINTER(wave2d_exact), _D, _D, _P]),
 }
 
 _lib = None
@@ -126,6 +129,19 @@ def launch_count() -> int:
 
 def lambda_max(scheme: int, conventional: bool = False) -> float:
     return lib().wave2d_lambda_max(scheme, int(conventional))
+
+
+def error_norms_noalloc(field_ptr: int, dtype: int, nx: int, ny: int, ld: int, h: float, c: float,
+                        t: float, ex: wave2d_exact | None = None, stream: int = 0):
+    """(rel_l2, rel_linf) of a caller-owned device field through the
+    allocation-free entry point (see include/wave2d.h)."""
+    l2, linf = ctypes.c_double(), ctypes.c_double()
+    check(lib().wave2d_error_norms_noalloc(ctypes.c_void_p(int(field_ptr)), int(dtype), int(nx), int(ny),
+                                           int(ld), float(h), float(c), float(t),
+                                           ctypes.byref(ex) if ex is not None else None,
+                                           ctypes.byref(l2), ctypes.byref(linf),
+                                           ctypes.c_void_p(int(stream) if stream else 0)))
+    return l2.value, linf.value
 
 
 # ----------------------------------------------------------------- allocator
