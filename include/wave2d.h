@@ -124,6 +124,10 @@ typedef struct {
     int32_t temporal_t;   /* steps per launch for WAVE2D_KERNEL_TEMPORAL; 0 = auto */
     int32_t use_graph;    /* capture runs of steps in a CUDA graph: 1 on, 0 off,
                              -1 automatic                                         */
+    int32_t ctas_per_sm;  /* resident CTAs per SM for the TMA kernels; 0 = auto:
+                             as many as fit while both levels nearly fit in L2,
+                             else one (measured: wider residency starves some
+                             CTAs once the levels stream from HBM)               */
 } wave2d_tune;
 
 typedef struct {

@@ -12,8 +12,8 @@
 // on every side in a row-major plane of `pitch` elements per row and ny + 2G
 // rows; node (i, j) lives at (j + G) * pitch + (i + G).  Zero boundary: the
 // ring holds zeros and is never written.  Periodic boundary: every kernel that
-// writes a node within G of an edge also writes its periodic images into the
-// ring, so readers never wrap indices.
+// writes a node within R (the stencil radius) of an edge also writes its
+// periodic images into the first R rings, so readers never wrap indices.
 #pragma once
 #include <cuda.h>
 #include <cuda_runtime.h>
@@ -80,21 +80,51 @@ struct St<DT_F32X2> {
     }
 };
 
-// Periodic images of node (i, j) inside the ghost ring.
+// Periodic images of node (i, j) in the first gw rings of ghosts.  A kernel
+// that advances one level reads at most R nodes away, so writers pass
+// gw = R (gw <= G): only nodes within R of an edge have images to write.
 template <int DT>
 __device__ __forceinline__ void write_images(const Level& L, const Geo& g, int i, int j,
-                                             typename St<DT>::V v) {
-    if (i >= g.G && i < g.nx - g.G && j >= g.G && j < g.ny - g.G) return;
-    const int mxr = (g.G + g.nx - 1) / g.nx, myr = (g.G + g.ny - 1) / g.ny;
+                                             typename St<DT>::V v, int gw) {
+    if (i >= gw && i < g.nx - gw && j >= gw && j < g.ny - gw) return;
+    const int mxr = (gw + g.nx - 1) / g.nx, myr = (gw + g.ny - 1) / g.ny;
     for (int my = -myr; my <= myr; ++my) {
         const int jj = j + my * g.ny;
-        if (jj < -g.G || jj >= g.ny + g.G) continue;
+        if (jj < -gw || jj >= g.ny + gw) continue;
         for (int mx = -mxr; mx <= mxr; ++mx) {
             if (mx == 0 && my == 0) continue;
             const int ii = i + mx * g.nx;
-            if (ii < -g.G || ii >= g.nx + g.G) continue;
+            if (ii < -gw || ii >= g.nx + gw) continue;
             St<DT>::st(L, off(g, ii, jj), v);
         }
+    }
+}
+
+// Periodic images of a whole aligned vector of VEC nodes (x a multiple of
+// VEC).  Valid when nx is a multiple of VEC, nx >= 2 VEC and ny >= 2 R: then
+// a node within R of an edge has exactly one image per wrapped direction,
+// and the image of the vector starting at x = 0 (x = nx - VEC) is the vector
+// at column nx (-VEC), which lies in the ghost ring because G >= VEC.  Images
+// of the vector's other nodes are written too; they are equally correct.
+template <typename VT>
+__device__ __forceinline__ void store_vec_images(VT* base, const Geo& g, int x, int y, VT v, int R,
+                                                 int vec) {
+    const bool ylo = y < R, yhi = y >= g.ny - R;
+    const bool xlo = x == 0, xhi = x + vec == g.nx;
+    if (!(ylo || yhi || xlo || xhi)) return;
+    const long long P = g.pitch;
+    auto at = [&](int xx, int yy) { return base + ((long long)(yy + g.G) * P + (xx + g.G)) / vec; };
+    if (ylo) *at(x, y + g.ny) = v;
+    if (yhi) *at(x, y - g.ny) = v;
+    if (xlo) {
+        *at(x + g.nx, y) = v;
+        if (ylo) *at(x + g.nx, y + g.ny) = v;
+        if (yhi) *at(x + g.nx, y - g.ny) = v;
+    }
+    if (xhi) {
+        *at(x - g.nx, y) = v;
+        if (ylo) *at(x - g.nx, y + g.ny) = v;
+        if (yhi) *at(x - g.nx, y - g.ny) = v;
     }
 }
 
@@ -284,8 +314,9 @@ __global__ void __launch_bounds__(256) k1_first_step(const double* __restrict__ 
         T::st(L0, o, q0);
         T::st(L1, o, q1);
         if (PER) {
-            write_images<DT>(L0, g, i, j, q0);
-            write_images<DT>(L1, g, i, j, q1);
+            constexpr int R = (S == 13) ? 2 : 1;
+            write_images<DT>(L0, g, i, j, q0, R);
+            write_images<DT>(L1, g, i, j, q1, R);
         }
         if (TRACK) error_terms(T::to_d(q1), exact_at(ex, i, j), s0, s1, m0, m1, rd.status);
     }
@@ -328,7 +359,7 @@ __global__ void __launch_bounds__(256) k2_simple(Level cur, Level nxt, Geo g,
         const V p = T::ld(nxt, o);
         const V r = two_step_update<S>(u, p, a);
         T::st(nxt, o, r);
-        if (PER) write_images<DT>(nxt, g, i, j, r);
+        if (PER) write_images<DT>(nxt, g, i, j, r, (S == 13) ? 2 : 1);
         if (TRACK) error_terms(T::to_d(r), exact_at(ex, i, j), s0, s1, m0, m1, rd.status);
     }
     if (TRACK) reduce_finalize<256>(s0, s1, m0, m1, rd);
@@ -358,12 +389,12 @@ __global__ void __launch_bounds__(256) k_pack(Level L, Geo g, double* __restrict
 }
 
 template <int DT, bool PER>
-__global__ void __launch_bounds__(256) k_unpack(const double* __restrict__ in, Level L, Geo g) {
+__global__ void __launch_bounds__(256) k_unpack(const double* __restrict__ in, Level L, Geo g, int gw) {
     const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y;
     if (i < g.nx && j < g.ny) {
         const typename St<DT>::V v = St<DT>::from_d(in[(size_t)j * g.nx + i]);
         St<DT>::st(L, off(g, i, j), v);
-        if (PER) write_images<DT>(L, g, i, j, v);
+        if (PER) write_images<DT>(L, g, i, j, v, gw);
     }
 }
 
@@ -538,8 +569,9 @@ __global__ void __launch_bounds__(NW * 32, 1)
         const int tx = t % tiles_x, ty = t / tiles_x;
         const int x = tx * TW + lane * VEC;  // first column of this lane's vector
         const int r0 = warp * RPW;            // first output row of this warp (tile coords)
-        const bool edge = PER && (tx * TW < g.G || tx * TW + TW > g.nx - g.G || ty * TH < g.G ||
-                                  ty * TH + TH > g.ny - g.G);
+        const bool edge = PER && (tx * TW < R || tx * TW + TW > g.nx - R || ty * TH < R ||
+                                  ty * TH + TH > g.ny - R);
+        const bool vec_images = (g.nx % VEC == 0) && g.nx >= 2 * VEC && g.ny >= 2 * R;
 
         // register window: win[q] holds tile row (r - R + q) of u^k
         RowBuf<T, VEC> win[2 * R + 1];
@@ -589,21 +621,32 @@ __global__ void __launch_bounds__(NW * 32, 1)
                 T* gp = nxt + off(g, x, y);
                 if (x + VEC <= g.nx) {
                     if constexpr (VEC == 4) {
-                        *reinterpret_cast<float4*>(gp) = make_float4(out[0], out[1], out[2], out[3]);
+                        const float4 v = make_float4(out[0], out[1], out[2], out[3]);
+                        *reinterpret_cast<float4*>(gp) = v;
+                        if (edge && vec_images) store_vec_images(reinterpret_cast<float4*>(nxt), g, x, y, v, R, 4);
                     } else {
-                        *reinterpret_cast<double2*>(gp) = make_double2(out[0], out[1]);
+                        const double2 v = make_double2(out[0], out[1]);
+                        *reinterpret_cast<double2*>(gp) = v;
+                        if (edge && vec_images) store_vec_images(reinterpret_cast<double2*>(nxt), g, x, y, v, R, 2);
                     }
                 } else {
 #pragma unroll
                     for (int e = 0; e < VEC; ++e)
                         if (x + e < g.nx) gp[e] = out[e];
                 }
-                if (edge) {
-                    const Level L{nxt, nullptr};
-#pragma unroll
-                    for (int e = 0; e < VEC; ++e)
-                        if (x + e < g.nx) write_images<DT>(L, g, x + e, y, out[e]);
-                }
+            }
+        }
+        if (edge && !vec_images) {
+            // Grids too small or not a multiple of the vector width: images
+            // node by node, in a rolled loop that re-reads the stored values.
+            const Level L{nxt, nullptr};
+#pragma unroll 1
+            for (int r = 0; r < RPW; ++r) {
+                const int y = ty * TH + r0 + r;
+                if (y >= g.ny) break;
+#pragma unroll 1
+                for (int e = 0; e < VEC; ++e)
+                    if (x + e < g.nx) write_images<DT>(L, g, x + e, y, nxt[off(g, x + e, y)], R);
             }
         }
         __syncthreads();  // every warp is done with stage s

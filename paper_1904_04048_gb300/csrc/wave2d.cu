@@ -350,7 +350,10 @@ static int launch_tma_t(wave2d* h) {
     const int tiles_x = (h->nx + C::TW - 1) / C::TW;
     const int tiles_y = (h->ny + TH - 1) / TH;
     const int n_tiles = tiles_x * tiles_y;
-    const int grid = std::min(n_tiles, occ * h->num_sms);
+    int per_sm = h->tune.ctas_per_sm;
+    if (per_sm <= 0) per_sm = (2.0 * (double)h->plane_bytes <= 1.25 * (double)h->l2_bytes) ? occ : 1;
+    per_sm = std::max(1, std::min(per_sm, occ));
+    const int grid = std::min(n_tiles, per_sm * h->num_sms);
     kern<<<grid, kTmaNW * 32, smem, h->stream>>>(h->tm_cur[h->cur], h->tm_prev[1 - h->cur],
                                                  reinterpret_cast<T*>(h->hi[1 - h->cur]), h->geo(),
                                                  coef_as<T>(h->a), tiles_x, n_tiles, h->status);
@@ -541,6 +544,7 @@ int wave2d_create(const wave2d_grid* grid, double hh, double tau, double c, int 
 
     cudaError_t e = cudaGetDevice(&h->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->l2_bytes, cudaDevAttrL2CacheSize, h->device);
     if (e != cudaSuccess) {
         delete h;
         return cuda_fail(e, "no usable CUDA device");
@@ -615,6 +619,8 @@ int wave2d_set_tuning(wave2d_t h, const wave2d_tune* tune) {
         return set_error(WAVE2D_ERR_ARG, "unknown kernel %d", tune->kernel);
     if (tune->kernel == WAVE2D_KERNEL_TMA && h->dtype == WAVE2D_F32X2)
         return set_error(WAVE2D_ERR_ARG, "the TMA kernel supports F32 and F64 storage only");
+    if (tune->ctas_per_sm < 0 || tune->ctas_per_sm > 32)
+        return set_error(WAVE2D_ERR_ARG, "ctas_per_sm must be 0 (auto) or 1..32");
     h->tune = *tune;
     return select_kernel(h);
 }
@@ -797,8 +803,8 @@ int wave2d_set_state(wave2d_t h, const double* u_prev, const double* u_cur, int6
     dispatch_dt(h->dtype, [&](auto DTc) {
         constexpr int DT = decltype(DTc)::value;
         dispatch_bool(h->bc == WAVE2D_BC_PERIODIC, [&](auto Pc) {
-            k_unpack<DT, decltype(Pc)::value><<<grid2d(h), dim3(32, 8), 0, h->stream>>>(dp, h->level(1), h->geo());
-            k_unpack<DT, decltype(Pc)::value><<<grid2d(h), dim3(32, 8), 0, h->stream>>>(dc, h->level(0), h->geo());
+            k_unpack<DT, decltype(Pc)::value><<<grid2d(h), dim3(32, 8), 0, h->stream>>>(dp, h->level(1), h->geo(), h->R);
+            k_unpack<DT, decltype(Pc)::value><<<grid2d(h), dim3(32, 8), 0, h->stream>>>(dc, h->level(0), h->geo(), h->R);
         });
     });
     cudaError_t e = cudaGetLastError();

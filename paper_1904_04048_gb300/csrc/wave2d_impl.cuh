@@ -41,7 +41,7 @@ struct wave2d {
     double h = 0, tau = 0, c = 0, lam = 0, lam_max = 0;
     double a[3] = {0, 0, 0}, b[3] = {0, 0, 0};
     // device
-    int device = 0, num_sms = 0;
+    int device = 0, num_sms = 0, l2_bytes = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     w2d::Allocator alloc;

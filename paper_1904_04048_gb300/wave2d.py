@@ -49,7 +49,7 @@ class wave2d_grid(ctypes.Structure):
 
 class wave2d_tune(ctypes.Structure):
     _fields_ = [("kernel", ctypes.c_int32), ("tile_h", ctypes.c_int32), ("temporal_t", ctypes.c_int32),
-                ("use_graph", ctypes.c_int32)]
+                ("use_graph", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32)]
 
 
 class wave2d_info_t(ctypes.Structure):
@@ -280,8 +280,8 @@ class Wave2D:
         buf = np.ascontiguousarray(buf, dtype=np.uint8)
         check(lib().wave2d_set_raw(self._h, buf.ctypes.data_as(ctypes.c_void_p), buf.size, int(k)))
 
-    def set_tuning(self, kernel=KERNEL_AUTO, tile_h=0, temporal_t=0, use_graph=-1):
-        t = wave2d_tune(int(kernel), int(tile_h), int(temporal_t), int(use_graph))
+    def set_tuning(self, kernel=KERNEL_AUTO, tile_h=0, temporal_t=0, use_graph=-1, ctas_per_sm=0):
+        t = wave2d_tune(int(kernel), int(tile_h), int(temporal_t), int(use_graph), int(ctas_per_sm))
         check(lib().wave2d_set_tuning(self._h, ctypes.byref(t)))
 
     def info(self) -> wave2d_info_t:
