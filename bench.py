@@ -46,7 +46,7 @@ WORKLOAD = ("9-point + 13-point schemes, FP32 storage, 4096^2 periodic grid, lam
 # benchmark size, from an ncu capture of the same kernel source (see the
 # profiles directory).  Keyed by a hash of the kernel sources so that the
 # figure is dropped once the kernel changes.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {"1191299771d313cb": 155738368}
 
 
 def kernel_source_hash() -> str:
