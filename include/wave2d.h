@@ -208,6 +208,17 @@ int wave2d_get_raw(wave2d_t h, void *dst, int64_t bytes, int64_t *k);
 int wave2d_set_raw(wave2d_t h, const void *src, int64_t bytes, int64_t k);
 
 int wave2d_set_tuning(wave2d_t h, const wave2d_tune *tune);
+
+/* Autotuner: time every candidate two-step configuration for `steps` levels
+ * on a copy of the current state (FP32: the TMA one-step kernel at 1 and 2
+ * CTAs per SM and the temporal kernel with T in {2, 4} and 32 or 64 rows per
+ * tile; FP64: TMA at 1 and 2 CTAs per SM and the one-node kernel), restore
+ * the state exactly (levels, k) and keep the fastest configuration, which is
+ * also written to *best (may be NULL).  Results do not depend on the choice:
+ * every configuration evaluates each node identically.  Needs an initialised
+ * handle (WAVE2D_ERR_STATE) and steps >= 1; allocates a snapshot of two
+ * levels for the duration of the call.  Synchronises the stream. */
+int wave2d_autotune(wave2d_t h, int64_t steps, wave2d_tune *best);
 int wave2d_get_info(wave2d_t h, wave2d_info_t *info);
 int wave2d_sync(wave2d_t h);
 void wave2d_destroy(wave2d_t h);

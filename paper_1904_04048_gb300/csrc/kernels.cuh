@@ -12,8 +12,9 @@
 // on every side in a row-major plane of `pitch` elements per row and ny + 2G
 // rows; node (i, j) lives at (j + G) * pitch + (i + G).  Zero boundary: the
 // ring holds zeros and is never written.  Periodic boundary: every kernel that
-// writes a node within R (the stencil radius) of an edge also writes its
-// periodic images into the first R rings, so readers never wrap indices.
+// writes a node within gw of an edge also writes its periodic images into the
+// first gw rings (gw = R, the stencil radius, for one-level kernels; deeper
+// when temporal blocking reads a wider halo), so readers never wrap indices.
 #pragma once
 #include <cuda.h>
 #include <cuda_runtime.h>
@@ -100,17 +101,17 @@ __device__ __forceinline__ void write_images(const Level& L, const Geo& g, int i
     }
 }
 
-// Periodic images of a whole aligned vector of VEC nodes (x a multiple of
-// VEC).  Valid when nx is a multiple of VEC, nx >= 2 VEC and ny >= 2 R: then
-// a node within R of an edge has exactly one image per wrapped direction,
-// and the image of the vector starting at x = 0 (x = nx - VEC) is the vector
-// at column nx (-VEC), which lies in the ghost ring because G >= VEC.  Images
-// of the vector's other nodes are written too; they are equally correct.
+// Periodic images of a whole aligned vector of `vec` nodes (x a multiple of
+// vec) in the first gw ghost rings.  Valid when nx is a multiple of vec and
+// nx, ny >= 2 gw: a node within gw of an edge then has exactly one image per
+// wrapped direction, and the images of an aligned vector are aligned vectors
+// inside the ring (gw <= G).  Images of the vector's other nodes are written
+// too; they are equally correct.
 template <typename VT>
-__device__ __forceinline__ void store_vec_images(VT* base, const Geo& g, int x, int y, VT v, int R,
+__device__ __forceinline__ void store_vec_images(VT* base, const Geo& g, int x, int y, VT v, int gw,
                                                  int vec) {
-    const bool ylo = y < R, yhi = y >= g.ny - R;
-    const bool xlo = x == 0, xhi = x + vec == g.nx;
+    const bool ylo = y < gw, yhi = y >= g.ny - gw;
+    const bool xlo = x < gw, xhi = x + vec > g.nx - gw;
     if (!(ylo || yhi || xlo || xhi)) return;
     const long long P = g.pitch;
     auto at = [&](int xx, int yy) { return base + ((long long)(yy + g.G) * P + (xx + g.G)) / vec; };
@@ -300,7 +301,7 @@ __global__ void __launch_bounds__(256) k1_first_step(const double* __restrict__ 
                                                      const double* __restrict__ v0, Level L0,
                                                      Level L1, Geo g, Coef3<double> ahalf,
                                                      Coef3<double> b, double tau, ExactTab ex,
-                                                     Reduce rd) {
+                                                     Reduce rd, int gw) {
     using T = St<DT>;
     const int i = blockIdx.x * 32 + threadIdx.x;
     const int j = blockIdx.y * 8 + threadIdx.y;
@@ -314,9 +315,8 @@ __global__ void __launch_bounds__(256) k1_first_step(const double* __restrict__ 
         T::st(L0, o, q0);
         T::st(L1, o, q1);
         if (PER) {
-            constexpr int R = (S == 13) ? 2 : 1;
-            write_images<DT>(L0, g, i, j, q0, R);
-            write_images<DT>(L1, g, i, j, q1, R);
+            write_images<DT>(L0, g, i, j, q0, gw);
+            write_images<DT>(L1, g, i, j, q1, gw);
         }
         if (TRACK) error_terms(T::to_d(q1), exact_at(ex, i, j), s0, s1, m0, m1, rd.status);
     }
@@ -329,7 +329,7 @@ __global__ void __launch_bounds__(256) k1_first_step(const double* __restrict__ 
 template <int DT, int S, bool PER, bool TRACK>
 __global__ void __launch_bounds__(256) k2_simple(Level cur, Level nxt, Geo g,
                                                  Coef3<typename St<DT>::V> a, ExactTab ex,
-                                                 Reduce rd) {
+                                                 Reduce rd, int gw) {
     using T = St<DT>;
     using V = typename T::V;
     const int i = blockIdx.x * 32 + threadIdx.x;
@@ -359,7 +359,7 @@ __global__ void __launch_bounds__(256) k2_simple(Level cur, Level nxt, Geo g,
         const V p = T::ld(nxt, o);
         const V r = two_step_update<S>(u, p, a);
         T::st(nxt, o, r);
-        if (PER) write_images<DT>(nxt, g, i, j, r, (S == 13) ? 2 : 1);
+        if (PER) write_images<DT>(nxt, g, i, j, r, gw);
         if (TRACK) error_terms(T::to_d(r), exact_at(ex, i, j), s0, s1, m0, m1, rd.status);
     }
     if (TRACK) reduce_finalize<256>(s0, s1, m0, m1, rd);
@@ -521,7 +521,7 @@ __device__ __forceinline__ RowBuf<T, NV> load_row(const T* row, int lane) {
 template <typename T, int S, bool PER, int TH, int NW, int NSTAGES>
 __global__ void __launch_bounds__(NW * 32, 1)
     k2_tma(const __grid_constant__ CUtensorMap tm_cur, const __grid_constant__ CUtensorMap tm_prev,
-           T* __restrict__ nxt, Geo g, Coef3<T> a, int tiles_x, int n_tiles, int* status) {
+           T* __restrict__ nxt, Geo g, Coef3<T> a, int tiles_x, int n_tiles, int gw, int* status) {
     using C = TmaCfg<T, S, TH, NW>;
     constexpr int VEC = C::VEC, R = C::R, TW = C::TW, BOX_W = C::BOX_W, RPW = C::RPW;
     constexpr int DT = sizeof(T) == 4 ? DT_F32 : DT_F64;
@@ -569,9 +569,9 @@ __global__ void __launch_bounds__(NW * 32, 1)
         const int tx = t % tiles_x, ty = t / tiles_x;
         const int x = tx * TW + lane * VEC;  // first column of this lane's vector
         const int r0 = warp * RPW;            // first output row of this warp (tile coords)
-        const bool edge = PER && (tx * TW < R || tx * TW + TW > g.nx - R || ty * TH < R ||
-                                  ty * TH + TH > g.ny - R);
-        const bool vec_images = (g.nx % VEC == 0) && g.nx >= 2 * VEC && g.ny >= 2 * R;
+        const bool edge = PER && (tx * TW < gw || tx * TW + TW > g.nx - gw || ty * TH < gw ||
+                                  ty * TH + TH > g.ny - gw);
+        const bool vec_images = (g.nx % VEC == 0) && g.nx >= 2 * gw && g.ny >= 2 * gw;
 
         // register window: win[q] holds tile row (r - R + q) of u^k
         RowBuf<T, VEC> win[2 * R + 1];
@@ -623,11 +623,11 @@ __global__ void __launch_bounds__(NW * 32, 1)
                     if constexpr (VEC == 4) {
                         const float4 v = make_float4(out[0], out[1], out[2], out[3]);
                         *reinterpret_cast<float4*>(gp) = v;
-                        if (edge && vec_images) store_vec_images(reinterpret_cast<float4*>(nxt), g, x, y, v, R, 4);
+                        if (edge && vec_images) store_vec_images(reinterpret_cast<float4*>(nxt), g, x, y, v, gw, 4);
                     } else {
                         const double2 v = make_double2(out[0], out[1]);
                         *reinterpret_cast<double2*>(gp) = v;
-                        if (edge && vec_images) store_vec_images(reinterpret_cast<double2*>(nxt), g, x, y, v, R, 2);
+                        if (edge && vec_images) store_vec_images(reinterpret_cast<double2*>(nxt), g, x, y, v, gw, 2);
                     }
                 } else {
 #pragma unroll
@@ -646,7 +646,7 @@ __global__ void __launch_bounds__(NW * 32, 1)
                 if (y >= g.ny) break;
 #pragma unroll 1
                 for (int e = 0; e < VEC; ++e)
-                    if (x + e < g.nx) write_images<DT>(L, g, x + e, y, nxt[off(g, x + e, y)], R);
+                    if (x + e < g.nx) write_images<DT>(L, g, x + e, y, nxt[off(g, x + e, y)], gw);
             }
         }
         __syncthreads();  // every warp is done with stage s

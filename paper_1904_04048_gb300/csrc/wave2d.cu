@@ -14,6 +14,7 @@
 #include <new>
 #include <vector>
 
+#include "kernels_temporal.cuh"
 #include "wave2d_impl.cuh"
 
 namespace w2d {
@@ -223,12 +224,33 @@ static int prepare_tma(wave2d* h) {
         if (h->dtype == DT_F32) tma_box<float, S, 32>(bw, bh, tw);
         else tma_box<double, S, 32>(bw, bh, tw);
     });
-    for (int p = 0; p < 2 && rc == WAVE2D_OK; ++p) {
+    for (int p = 0; p < h->nlevels && rc == WAVE2D_OK; ++p) {
         rc = encode_plane(&h->tm_cur[p], h->hi[p], h, bw, bh);
         if (rc == WAVE2D_OK) rc = encode_plane(&h->tm_prev[p], h->hi[p], h, tw, 32);
     }
     h->tma_ready = (rc == WAVE2D_OK);
     return rc;
+}
+
+// Temporal kernel: region width in vectors and warps per CTA.
+constexpr int kTempRVW = 64;
+constexpr int kTempNW = 8;
+
+static int prepare_temporal(wave2d* h) {
+    const int key = h->scheme * 10000 + h->temporal_oh * 10 + h->temporal_t;
+    if (h->reg_key == key) return WAVE2D_OK;
+    int rh = 0;
+    dispatch_s(h->scheme, [&](auto Sc) {
+        constexpr int S = decltype(Sc)::value;
+        constexpr int R = (S == 13) ? 2 : 1;
+        rh = h->temporal_oh + 2 * R * h->temporal_t;
+    });
+    for (int p = 0; p < h->nlevels; ++p) {
+        int rc = encode_plane(&h->tm_reg[p], h->hi[p], h, 4 * kTempRVW, rh);
+        if (rc != WAVE2D_OK) return rc;
+    }
+    h->reg_key = key;
+    return WAVE2D_OK;
 }
 
 // ------------------------------------------------------------ exact tables
@@ -300,7 +322,7 @@ static int launch_first_step(wave2d* h, const double* du0, const double* dv0) {
                 dispatch_bool(h->tracking, [&](auto Tc) {
                     k1_first_step<decltype(DTc)::value, decltype(Sc)::value, decltype(Pc)::value,
                                   decltype(Tc)::value><<<grid2d(h), dim3(32, 8), 0, h->stream>>>(
-                        du0, dv0, L0, L1, h->geo(), ca, cb, h->tau, ex, rd);
+                        du0, dv0, L0, L1, h->geo(), ca, cb, h->tau, ex, rd, h->gw);
                 });
             });
         });
@@ -310,7 +332,7 @@ static int launch_first_step(wave2d* h, const double* du0, const double* dv0) {
 }
 
 static int launch_simple_step(wave2d* h, bool track) {
-    const Level cur = h->level(h->cur), nxt = h->level(1 - h->cur);
+    const Level cur = h->level(h->cur), nxt = h->level(h->prv);
     const ExactTab ex = track ? make_tab(h, h->tab_track, h->track_ex, (double)(h->k + 1) * h->tau) : ExactTab{};
     const Reduce rd = make_reduce(h, h->acc_track, 1);
     dispatch_dt(h->dtype, [&](auto DTc) {
@@ -321,7 +343,7 @@ static int launch_simple_step(wave2d* h, bool track) {
             dispatch_bool(h->bc == WAVE2D_BC_PERIODIC, [&](auto Pc) {
                 dispatch_bool(track, [&](auto Tc) {
                     k2_simple<DT, decltype(Sc)::value, decltype(Pc)::value, decltype(Tc)::value>
-                        <<<grid2d(h), dim3(32, 8), 0, h->stream>>>(cur, nxt, h->geo(), a, ex, rd);
+                        <<<grid2d(h), dim3(32, 8), 0, h->stream>>>(cur, nxt, h->geo(), a, ex, rd, h->gw);
                 });
             });
         });
@@ -354,9 +376,9 @@ static int launch_tma_t(wave2d* h) {
     if (per_sm <= 0) per_sm = (2.0 * (double)h->plane_bytes <= 1.25 * (double)h->l2_bytes) ? occ : 1;
     per_sm = std::max(1, std::min(per_sm, occ));
     const int grid = std::min(n_tiles, per_sm * h->num_sms);
-    kern<<<grid, kTmaNW * 32, smem, h->stream>>>(h->tm_cur[h->cur], h->tm_prev[1 - h->cur],
-                                                 reinterpret_cast<T*>(h->hi[1 - h->cur]), h->geo(),
-                                                 coef_as<T>(h->a), tiles_x, n_tiles, h->status);
+    kern<<<grid, kTmaNW * 32, smem, h->stream>>>(h->tm_cur[h->cur], h->tm_prev[h->prv],
+                                                 reinterpret_cast<T*>(h->hi[h->prv]), h->geo(),
+                                                 coef_as<T>(h->a), tiles_x, n_tiles, h->gw, h->status);
     W2D_LAUNCHED("TMA two-step kernel launch");
     return WAVE2D_OK;
 }
@@ -373,13 +395,77 @@ static int launch_tma_step(wave2d* h) {
     return rc;
 }
 
-static int launch_one_step(wave2d* h) {
+// T two-steps in one launch, out of place into the other pair of planes.
+template <int S, bool PER, int OH, int T>
+static int launch_temporal_t(wave2d* h) {
+    using C = TemporalCfg<S, kTempRVW, OH, T>;
+    auto kern = k3_temporal<S, PER, kTempRVW, OH, T, kTempNW>;
+    const int smem = 1024 + 2 * C::BUF_BYTES;
+    static thread_local bool configured = false;  // per instantiation
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(temporal kernel)");
+        configured = true;
+    }
+    // The levels move to the other pair with their roles kept (plane p -> p ^ 2),
+    // so two launches bring every level back to its plane.
+    const int oc = h->cur ^ 2, op = h->prv ^ 2;
+    const int tiles_x = (h->nx + C::OW - 1) / C::OW;
+    const int tiles_y = (h->ny + OH - 1) / OH;
+    kern<<<tiles_x * tiles_y, kTempNW * 32, smem, h->stream>>>(
+        h->tm_reg[h->cur], h->tm_reg[h->prv], reinterpret_cast<float*>(h->hi[oc]),
+        reinterpret_cast<float*>(h->hi[op]), h->geo(), coef_as<float>(h->a), tiles_x, h->gw, h->status);
+    W2D_LAUNCHED("temporal two-step kernel launch");
+    h->cur = oc;
+    h->prv = op;
+    return WAVE2D_OK;
+}
+
+static int launch_temporal(wave2d* h) {
+    int rc = WAVE2D_OK;
+    dispatch_s(h->scheme, [&](auto Sc) {
+        constexpr int S = decltype(Sc)::value;
+        dispatch_bool(h->bc == WAVE2D_BC_PERIODIC, [&](auto Pc) {
+            constexpr bool P = decltype(Pc)::value;
+            const int T = h->temporal_t, OH = h->temporal_oh;
+            if (T == 2 && OH == 32) rc = launch_temporal_t<S, P, 32, 2>(h);
+            else if (T == 2) rc = launch_temporal_t<S, P, 64, 2>(h);
+            else if (OH == 32) rc = launch_temporal_t<S, P, 32, 4>(h);
+            else rc = launch_temporal_t<S, P, 64, 4>(h);
+        });
+    });
+    return rc;
+}
+
+// Advance by one launch: T levels for the temporal kernel when at least T
+// remain, else one level.  Returns the number of levels advanced (< 0: error).
+static int launch_block(wave2d* h, int64_t remaining) {
     int rc;
-    if (h->kernel == WAVE2D_KERNEL_TMA) rc = launch_tma_step(h);
+    if (h->kernel == WAVE2D_KERNEL_TEMPORAL && remaining >= h->temporal_t) {
+        rc = launch_temporal(h);
+        if (rc != WAVE2D_OK) return rc;
+        h->k += h->temporal_t;
+        return h->temporal_t;
+    }
+    if (h->kernel == WAVE2D_KERNEL_TMA || h->kernel == WAVE2D_KERNEL_TEMPORAL) rc = launch_tma_step(h);
     else rc = launch_simple_step(h, false);
     if (rc != WAVE2D_OK) return rc;
-    h->cur = 1 - h->cur;
+    std::swap(h->cur, h->prv);
     h->k += 1;
+    return 1;
+}
+
+// Rewrite the periodic images of the current two levels in the first gw rings.
+static int refresh_ghosts(wave2d* h) {
+    if (h->bc != WAVE2D_BC_PERIODIC || !h->initialized) return WAVE2D_OK;
+    const long long total = (long long)(h->nx + 2 * h->gw) * (h->ny + 2 * h->gw);
+    const int grid = (int)std::min<long long>((total + 255) / 256, 8LL * h->num_sms);
+    for (int p : {h->cur, h->prv}) {
+        dispatch_dt(h->dtype, [&](auto DTc) {
+            k_refresh_ghosts<decltype(DTc)::value><<<grid, 256, 0, h->stream>>>(h->level(p), h->geo(), h->gw);
+        });
+        W2D_LAUNCHED("ghost refresh kernel launch");
+    }
     return WAVE2D_OK;
 }
 
@@ -398,14 +484,26 @@ static int select_kernel(wave2d* h) {
         want = (h->dtype != DT_F32X2 && (int64_t)h->nx * h->ny >= 65536) ? WAVE2D_KERNEL_TMA
                                                                          : WAVE2D_KERNEL_SIMPLE;
     }
-    if (want == WAVE2D_KERNEL_TEMPORAL) want = WAVE2D_KERNEL_TMA;  // not built yet: fall to one step
+    if (want == WAVE2D_KERNEL_TEMPORAL && h->dtype != DT_F32) want = WAVE2D_KERNEL_TMA;
     if (want == WAVE2D_KERNEL_TMA && h->dtype == DT_F32X2) want = WAVE2D_KERNEL_SIMPLE;
-    if (want == WAVE2D_KERNEL_TMA && !h->tma_ready) {
+    if ((want == WAVE2D_KERNEL_TMA || want == WAVE2D_KERNEL_TEMPORAL) && !h->tma_ready) {
         int rc = prepare_tma(h);
         if (rc != WAVE2D_OK) return rc;
     }
+    if (want == WAVE2D_KERNEL_TEMPORAL) {
+        h->temporal_t = h->tune.temporal_t > 0 ? h->tune.temporal_t : 4;
+        h->temporal_oh = h->tune.tile_h > 0 ? h->tune.tile_h : 64;
+        int rc = prepare_temporal(h);
+        if (rc != WAVE2D_OK) return rc;
+    }
+    // Periodic images: one-level kernels read R nodes beyond an edge, the
+    // temporal kernel up to the full ghost ring.
+    const int gw = (want == WAVE2D_KERNEL_TEMPORAL) ? h->G : h->R;
+    const bool deeper = gw > h->gw;
+    h->gw = gw;
     h->kernel = want;
     drop_graphs(h);
+    if (deeper) return refresh_ghosts(h);
     return WAVE2D_OK;
 }
 
@@ -417,33 +515,60 @@ static bool want_graph(const wave2d* h, int64_t n) {
 
 constexpr int kGraphSteps = 32;
 
+// A graph of kGraphSteps levels (a multiple of 2 T) returns the levels to the
+// planes they started in, so one graph per starting (cur, prv) is replayed.
 static int run_graph(wave2d* h, int64_t& n) {
-    if (!h->graph[h->cur]) {
-        const int cur0 = h->cur;
+    const int key = h->cur * 4 + h->prv;
+    static_assert(kGraphSteps % 8 == 0, "graph length must be a multiple of 2T");
+    if (!h->graph[key]) {
+        const int cur0 = h->cur, prv0 = h->prv;
         const int64_t k0 = h->k;
         cudaGraph_t g = nullptr;
         W2D_CUDA(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
         const int64_t before = g_launches.load();
+        int64_t done = 0;
         int rc = WAVE2D_OK;
-        for (int s = 0; s < kGraphSteps && rc == WAVE2D_OK; ++s) rc = launch_one_step(h);
+        while (done < kGraphSteps) {
+            const int adv = launch_block(h, kGraphSteps - done);
+            if (adv < 0) {
+                rc = adv;
+                break;
+            }
+            done += adv;
+        }
+        const int64_t launched = g_launches.load() - before;
         cudaError_t e = cudaStreamEndCapture(h->stream, &g);
         g_launches.store(before);  // captured launches run only when the graph does
+        h->graph_end[key] = h->cur * 4 + h->prv;
         h->cur = cur0;
+        h->prv = prv0;
         h->k = k0;
         if (rc != WAVE2D_OK) {
             if (g) cudaGraphDestroy(g);
             return rc;
         }
         if (e != cudaSuccess) return cuda_fail(e, "end capture");
-        e = cudaGraphInstantiate(&h->graph[cur0], g, 0);
+        e = cudaGraphInstantiate(&h->graph[key], g, 0);
         cudaGraphDestroy(g);
         if (e != cudaSuccess) return cuda_fail(e, "graph instantiate");
-        h->graph_steps = kGraphSteps;
+        h->graph_steps = (int)launched;
+    }
+    if (h->graph_end[key] != key) {
+        // The captured run does not end where it started: replay it once.
+        if (n >= kGraphSteps) {
+            W2D_CUDA(cudaGraphLaunch(h->graph[key], h->stream), "graph launch");
+            g_launches.fetch_add(h->graph_steps);
+            h->cur = h->graph_end[key] / 4;
+            h->prv = h->graph_end[key] % 4;
+            h->k += kGraphSteps;
+            n -= kGraphSteps;
+        }
+        return WAVE2D_OK;
     }
     while (n >= kGraphSteps) {
-        W2D_CUDA(cudaGraphLaunch(h->graph[h->cur], h->stream), "graph launch");
-        g_launches.fetch_add(kGraphSteps);
-        h->k += kGraphSteps;  // even count: parity unchanged
+        W2D_CUDA(cudaGraphLaunch(h->graph[key], h->stream), "graph launch");
+        g_launches.fetch_add(h->graph_steps);
+        h->k += kGraphSteps;
         n -= kGraphSteps;
     }
     return WAVE2D_OK;
@@ -559,13 +684,17 @@ int wave2d_create(const wave2d_grid* grid, double hh, double tau, double c, int 
         h->own_stream = true;
     }
 
-    // Layout: level planes (2, or 4 for hi/lo), then scratch.
+    // Layout: level planes, then scratch.  FP32 keeps two pairs of levels
+    // (the temporal kernel writes out of place); FP32x2 keeps hi and lo
+    // planes of two levels; FP64 two levels.
     h->elem = (h->dtype == WAVE2D_F64) ? 8 : 4;
+    h->nlevels = (h->dtype == WAVE2D_F32) ? 4 : 2;
+    h->gw = h->R;
     h->G = kGhost;
     h->pitch = (int)round_up((size_t)h->nx + 2 * kGhost, 32);
     h->rows = h->ny + 2 * kGhost;
     h->plane_bytes = round_up((size_t)h->pitch * h->rows * h->elem, 1024);
-    const int nplanes = (h->dtype == WAVE2D_F32X2) ? 4 : 2;
+    const int nplanes = (h->dtype == WAVE2D_F32X2) ? 4 : h->nlevels;
     const size_t k2_blocks = (size_t)((h->nx + 31) / 32) * ((h->ny + 7) / 8);
     h->partial_blocks = std::max<size_t>(k2_blocks, 64 * 1024);
     const size_t tab_doubles = 2 * (size_t)h->nx + 2 * (size_t)h->ny;
@@ -579,8 +708,8 @@ int wave2d_create(const wave2d_grid* grid, double hh, double tau, double c, int 
         return set_error(WAVE2D_ERR_OOM, "device allocation of %zu bytes failed", h->base_bytes);
     }
     char* p = (char*)h->base;
-    for (int q = 0; q < 2; ++q) h->hi[q] = p + q * h->plane_bytes;
-    if (nplanes == 4)
+    for (int q = 0; q < h->nlevels; ++q) h->hi[q] = p + q * h->plane_bytes;
+    if (h->dtype == WAVE2D_F32X2)
         for (int q = 0; q < 2; ++q) h->lo[q] = p + (2 + q) * h->plane_bytes;
     p += nplanes * h->plane_bytes;
     h->partials = (double*)p;
@@ -648,7 +777,7 @@ int wave2d_get_info(wave2d_t h, wave2d_info_t* info) {
     info->ghost = h->G;
     info->device_bytes = (int64_t)h->base_bytes;
     info->kernel = h->kernel;
-    info->temporal_t = 1;
+    info->temporal_t = (h->kernel == WAVE2D_KERNEL_TEMPORAL) ? h->temporal_t : 1;
     return WAVE2D_OK;
 }
 
@@ -690,8 +819,10 @@ int wave2d_first_step(wave2d_t h, const double* u0, const double* v0, int on_dev
     if (stage) dev_free(h->alloc, stage, 2 * n * sizeof(double), h->stream);
     if (rc != WAVE2D_OK) return rc;
     h->cur = 0;  // plane 0 holds u^1, plane 1 holds u^0
+    h->prv = 1;
     h->k = 1;
     h->initialized = true;
+    drop_graphs(h);
     return WAVE2D_OK;
 }
 
@@ -703,7 +834,7 @@ int wave2d_step_n(wave2d_t h, int64_t n) {
         for (int64_t s = 0; s < n; ++s) {
             int rc = launch_simple_step(h, true);
             if (rc != WAVE2D_OK) return rc;
-            h->cur = 1 - h->cur;
+            std::swap(h->cur, h->prv);
             h->k += 1;
         }
         return WAVE2D_OK;
@@ -712,9 +843,10 @@ int wave2d_step_n(wave2d_t h, int64_t n) {
         int rc = run_graph(h, n);
         if (rc != WAVE2D_OK) return rc;
     }
-    for (int64_t s = 0; s < n; ++s) {
-        int rc = launch_one_step(h);
-        if (rc != WAVE2D_OK) return rc;
+    while (n > 0) {
+        const int adv = launch_block(h, n);
+        if (adv < 0) return adv;
+        n -= adv;
     }
     return WAVE2D_OK;
 }
@@ -768,7 +900,7 @@ int wave2d_get_state(wave2d_t h, double* u_prev, double* u_cur, int64_t* k) {
     if (!stage) return set_error(WAVE2D_ERR_OOM, "staging allocation failed");
     dispatch_dt(h->dtype, [&](auto DTc) {
         constexpr int DT = decltype(DTc)::value;
-        k_pack<DT><<<grid2d(h), dim3(32, 8), 0, h->stream>>>(h->level(1 - h->cur), h->geo(), stage);
+        k_pack<DT><<<grid2d(h), dim3(32, 8), 0, h->stream>>>(h->level(h->prv), h->geo(), stage);
         k_pack<DT><<<grid2d(h), dim3(32, 8), 0, h->stream>>>(h->level(h->cur), h->geo(), stage + n);
     });
     cudaError_t e = cudaGetLastError();
@@ -800,11 +932,12 @@ int wave2d_set_state(wave2d_t h, const double* u_prev, const double* u_cur, int6
         dc = stage + n;
     }
     h->cur = 0;
+    h->prv = 1;
     dispatch_dt(h->dtype, [&](auto DTc) {
         constexpr int DT = decltype(DTc)::value;
         dispatch_bool(h->bc == WAVE2D_BC_PERIODIC, [&](auto Pc) {
-            k_unpack<DT, decltype(Pc)::value><<<grid2d(h), dim3(32, 8), 0, h->stream>>>(dp, h->level(1), h->geo(), h->R);
-            k_unpack<DT, decltype(Pc)::value><<<grid2d(h), dim3(32, 8), 0, h->stream>>>(dc, h->level(0), h->geo(), h->R);
+            k_unpack<DT, decltype(Pc)::value><<<grid2d(h), dim3(32, 8), 0, h->stream>>>(dp, h->level(1), h->geo(), h->gw);
+            k_unpack<DT, decltype(Pc)::value><<<grid2d(h), dim3(32, 8), 0, h->stream>>>(dc, h->level(0), h->geo(), h->gw);
         });
     });
     cudaError_t e = cudaGetLastError();
@@ -829,7 +962,7 @@ int wave2d_get_raw(wave2d_t h, void* dst, int64_t bytes, int64_t* k) {
     if (!h->initialized) return set_error(WAVE2D_ERR_STATE, "no state yet");
     if (bytes < wave2d_raw_bytes(h)) return set_error(WAVE2D_ERR_ARG, "buffer too small");
     char* d = (char*)dst;
-    const int order[2] = {1 - h->cur, h->cur};
+    const int order[2] = {h->prv, h->cur};
     for (int q = 0; q < 2; ++q) {
         W2D_CUDA(cudaMemcpyAsync(d + q * h->plane_bytes, h->hi[order[q]], h->plane_bytes, cudaMemcpyDeviceToHost,
                                  h->stream),
@@ -850,6 +983,7 @@ int wave2d_set_raw(wave2d_t h, const void* src, int64_t bytes, int64_t k) {
     if (bytes < wave2d_raw_bytes(h)) return set_error(WAVE2D_ERR_ARG, "buffer too small");
     const char* s = (const char*)src;
     h->cur = 1;  // plane 0 <- u^{k-1}, plane 1 <- u^k
+    h->prv = 0;
     for (int q = 0; q < 2; ++q) {
         W2D_CUDA(cudaMemcpyAsync(h->hi[q], s + q * h->plane_bytes, h->plane_bytes, cudaMemcpyHostToDevice, h->stream),
                  "raw copy");
@@ -862,7 +996,104 @@ int wave2d_set_raw(wave2d_t h, const void* src, int64_t bytes, int64_t k) {
     h->k = k;
     h->initialized = true;
     drop_graphs(h);
-    return WAVE2D_OK;
+    return refresh_ghosts(h);  // the copied rings may come from a shallower mode
+}
+
+int wave2d_autotune(wave2d_t h, int64_t steps, wave2d_tune* best) {
+    if (!h) return set_error(WAVE2D_ERR_ARG, "null handle");
+    if (steps < 1) return set_error(WAVE2D_ERR_ARG, "autotune needs steps >= 1");
+    if (!h->initialized) return set_error(WAVE2D_ERR_STATE, "autotune needs an initialised state");
+    std::vector<wave2d_tune> cands;
+    auto add = [&](int kernel, int tile_h, int T, int per_sm) {
+        wave2d_tune t{};
+        t.kernel = kernel;
+        t.tile_h = tile_h;
+        t.temporal_t = T;
+        t.use_graph = -1;
+        t.ctas_per_sm = per_sm;
+        cands.push_back(t);
+    };
+    if (h->dtype == WAVE2D_F32) {
+        add(WAVE2D_KERNEL_TMA, 0, 0, 1);
+        add(WAVE2D_KERNEL_TMA, 0, 0, 2);
+        for (int T : {2, 4})
+            for (int oh : {32, 64}) add(WAVE2D_KERNEL_TEMPORAL, oh, T, 0);
+    } else if (h->dtype == WAVE2D_F64) {
+        add(WAVE2D_KERNEL_TMA, 0, 0, 1);
+        add(WAVE2D_KERNEL_TMA, 0, 0, 2);
+        add(WAVE2D_KERNEL_SIMPLE, 0, 0, 0);
+    } else {
+        add(WAVE2D_KERNEL_SIMPLE, 0, 0, 0);
+    }
+    if (h->tracking || cands.size() == 1) {
+        h->tune = cands[0];
+        int rc = select_kernel(h);
+        if (best) *best = h->tune;
+        return rc;
+    }
+    // Snapshot the two current levels (hi and lo planes).
+    const int np = h->lo[0] ? 2 : 1;
+    const size_t snap_bytes = 2 * (size_t)np * h->plane_bytes;
+    char* snap = (char*)dev_alloc(h->alloc, snap_bytes, h->stream);
+    if (!snap) return set_error(WAVE2D_ERR_OOM, "autotune snapshot allocation failed");
+    const int cur0 = h->cur, prv0 = h->prv;
+    const int64_t k0 = h->k;
+    auto copy_levels = [&](bool save) -> int {
+        const int planes[2] = {cur0, prv0};
+        for (int q = 0; q < 2; ++q)
+            for (int part = 0; part < np; ++part) {
+                void* dev = part == 0 ? h->hi[planes[q]] : h->lo[planes[q]];
+                char* sp = snap + ((size_t)q * np + part) * h->plane_bytes;
+                cudaError_t e = save ? cudaMemcpyAsync(sp, dev, h->plane_bytes, cudaMemcpyDeviceToDevice, h->stream)
+                                     : cudaMemcpyAsync(dev, sp, h->plane_bytes, cudaMemcpyDeviceToDevice, h->stream);
+                if (e != cudaSuccess) return cuda_fail(e, "autotune snapshot copy");
+            }
+        h->cur = cur0;
+        h->prv = prv0;
+        h->k = k0;
+        return WAVE2D_OK;
+    };
+    int rc = copy_levels(true);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (rc == WAVE2D_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
+        rc = set_error(WAVE2D_ERR_CUDA, "event create failed");
+    float best_ms = 0;
+    wave2d_tune chosen = cands[0];
+    for (size_t c = 0; c < cands.size() && rc == WAVE2D_OK; ++c) {
+        rc = copy_levels(false);
+        if (rc != WAVE2D_OK) break;
+        h->tune = cands[c];
+        rc = select_kernel(h);
+        if (rc == WAVE2D_OK) rc = refresh_ghosts(h);
+        if (rc == WAVE2D_OK) rc = wave2d_step_n(h, std::min<int64_t>(steps, 8));  // warm-up
+        if (rc != WAVE2D_OK) break;
+        cudaEventRecord(e0, h->stream);
+        rc = wave2d_step_n(h, steps);
+        cudaEventRecord(e1, h->stream);
+        if (rc != WAVE2D_OK) break;
+        if (cudaEventSynchronize(e1) != cudaSuccess) {
+            rc = set_error(WAVE2D_ERR_CUDA, "autotune timing failed");
+            break;
+        }
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (c == 0 || ms < best_ms) {
+            best_ms = ms;
+            chosen = cands[c];
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    const int rc_restore = copy_levels(false);
+    dev_free(h->alloc, snap, snap_bytes, h->stream);
+    if (rc == WAVE2D_OK) rc = rc_restore;
+    if (rc != WAVE2D_OK) return rc;
+    h->tune = chosen;
+    rc = select_kernel(h);
+    if (rc == WAVE2D_OK) rc = refresh_ghosts(h);
+    if (rc == WAVE2D_OK) rc = check_status(h);
+    if (best) *best = chosen;
+    return rc;
 }
 
 int wave2d_sync(wave2d_t h) {

@@ -49,8 +49,9 @@ struct wave2d {
     size_t elem = 0, plane_bytes = 0;
     void* base = nullptr;
     size_t base_bytes = 0;
-    void* hi[2] = {nullptr, nullptr};
-    void* lo[2] = {nullptr, nullptr};
+    void* hi[4] = {nullptr, nullptr, nullptr, nullptr};  // level planes (hi parts)
+    void* lo[4] = {nullptr, nullptr, nullptr, nullptr};  // lo parts (FP32x2 only)
+    int nlevels = 2;  // 4 for FP32: a second pair for the out-of-place temporal kernel
     // scratch
     double* partials = nullptr;
     size_t partial_blocks = 0;
@@ -61,7 +62,8 @@ struct wave2d {
     double* tab_eval = nullptr;   // 2 nx + 2 ny doubles
     double* tab_track = nullptr;  // 2 nx + 2 ny doubles
     // state
-    int cur = 0;  // plane holding u^k
+    int cur = 0, prv = 1;  // planes holding u^k and u^{k-1}
+    int gw = 1;            // periodic image rings kept valid by every writer
     int64_t k = 0;
     bool initialized = false;
     bool tracking = false;
@@ -70,11 +72,15 @@ struct wave2d {
     wave2d_tune tune{};
     int kernel = WAVE2D_KERNEL_SIMPLE;
     int tile_h = 32;
-    // TMA descriptors: [plane] for u^k (halo box) and u^{k-1} (tile box)
-    CUtensorMap tm_cur[2], tm_prev[2];
+    int temporal_t = 4, temporal_oh = 64;  // levels per launch and output rows per tile
+    // TMA descriptors per plane: u^k halo box and u^{k-1} tile box of the
+    // one-step kernel; region box of the temporal kernel (for reg_key)
+    CUtensorMap tm_cur[4], tm_prev[4], tm_reg[4];
     bool tma_ready = false;
-    // graph of an even number of steps per starting parity
-    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    int reg_key = -1;
+    // captured runs of steps, keyed by the starting (cur, prv) planes
+    cudaGraphExec_t graph[16] = {};
+    int graph_end[16] = {};  // (cur, prv) after a replay, as cur * 4 + prv
     int graph_steps = 0;
 
     w2d::Level level(int p) const { return w2d::Level{hi[p], lo[p]}; }

@@ -83,6 +83,7 @@ SIGNATURES = {
     "wave2d_get_raw": (ctypes.c_int, [_P, _P, ctypes.c_int64, _I64P]),
     "wave2d_set_raw": (ctypes.c_int, [_P, _P, ctypes.c_int64, ctypes.c_int64]),
     "wave2d_set_tuning": (ctypes.c_int, [_P, ctypes.POINTER(wave2d_tune)]),
+    "wave2d_autotune": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.POINTER(wave2d_tune)]),
     "wave2d_get_info": (ctypes.c_int, [_P, ctypes.POINTER(wave2d_info_t)]),
     "wave2d_sync": (ctypes.c_int, [_P]),
     "wave2d_destroy": (None, [_P]),
@@ -283,6 +284,11 @@ class Wave2D:
     def set_tuning(self, kernel=KERNEL_AUTO, tile_h=0, temporal_t=0, use_graph=-1, ctas_per_sm=0):
         t = wave2d_tune(int(kernel), int(tile_h), int(temporal_t), int(use_graph), int(ctas_per_sm))
         check(lib().wave2d_set_tuning(self._h, ctypes.byref(t)))
+
+    def autotune(self, steps=16) -> wave2d_tune:
+        best = wave2d_tune()
+        check(lib().wave2d_autotune(self._h, int(steps), ctypes.byref(best)))
+        return best
 
     def info(self) -> wave2d_info_t:
         inf = wave2d_info_t()
