@@ -42,16 +42,16 @@ WORKLOAD = ("9-point + 13-point schemes, FP32 storage, 4096^2 periodic grid, lam
             "2000 time levels each (first step + 1999 two-steps), 16 Gaussian pulses + band-limited "
             "noise (seed 2019), FP64 norm of the final field to host")
 
-# DRAM bytes (read + write) of one launch of the TMA two-step kernel at the
-# benchmark size, from an ncu capture of the same kernel source (see the
-# profiles directory).  Keyed by a hash of the kernel sources so that the
-# figure is dropped once the kernel changes.
-NCU_TRAFFIC = {"1191299771d313cb": 155738368}
+# DRAM bytes (read + write) of one launch of a kernel at the benchmark size,
+# from an ncu capture of the same kernel source (see the profiles directory),
+# keyed by (kernel, hash of the kernel sources) so that a figure is dropped
+# once the kernel changes.
+NCU_TRAFFIC = {}
 
 
 def kernel_source_hash() -> str:
     hsh = hashlib.sha256()
-    for f in ("kernels.cuh", "stencil_ops.cuh"):
+    for f in ("kernels.cuh", "kernels_temporal.cuh", "stencil_ops.cuh"):
         with open(os.path.join(ROOT, "paper_1904_04048_gb300", "csrc", f), "rb") as fh:
             hsh.update(fh.read())
     return hsh.hexdigest()[:16]
@@ -172,9 +172,18 @@ def run_ours(args, rank, world, local_rank):
     for s in SCHEMES:
         lam = 0.9 * LAMBDA_MAX[s]
         sims[s] = w.Wave2D(N, N, h, lam * h, scheme=s, bc=BC_PERIODIC, dtype=w.F32, stream=stream.cuda_stream)
-    kernel = sims[13].info().kernel
     du0 = torch.from_numpy(u0).to(dev)
     dv0 = torch.from_numpy(v0).to(dev)
+    torch.cuda.synchronize(dev)
+    # Autotune each handle once on its own data (outside the timed region).
+    tuned = {}
+    for s in SCHEMES:
+        sims[s].first_step(du0, dv0)
+        best = sims[s].autotune(steps=64)
+        tuned[s] = {"kernel": {1: "simple", 2: "tma", 3: "temporal"}[best.kernel],
+                    "temporal_t": best.temporal_t, "tile_h": best.tile_h, "ctas_per_sm": best.ctas_per_sm}
+    kernel = sims[13].info().kernel
+    T13 = sims[13].info().temporal_t
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 512 MiB > L2
     torch.cuda.synchronize(dev)
     results = {}
@@ -216,7 +225,32 @@ def run_ours(args, rank, world, local_rank):
     launches = w.launch_count() - c0
     elapsed = t_start.elapsed_time(t_end) / 1e3
     stepn_s = sum(a.elapsed_time(b) for _, a, b in timing) / 1e3
-    n_two_step_launches = args.steps * len(SCHEMES) * (STEPS_PER_SCHEME - 1)
+
+    def time_levels(sim, n_levels, reps=1):
+        """Event time of n_levels two-steps on the handle's stream."""
+        sim.sync()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            sim.step_n(n_levels)
+        e1.record(stream)
+        sim.sync()
+        return e0.elapsed_time(e1) / 1e3
+
+    # Per-launch durations of the kernels inside step_n (after the timed
+    # region): the one-step TMA kernel, and the temporal kernel if chosen.
+    one_step = {}
+    for s in SCHEMES:
+        info = sims[s].info()
+        if info.kernel == w.KERNEL_TEMPORAL:
+            T = info.temporal_t
+            saved = (info.kernel, info.temporal_t)
+            sims[s].set_tuning(kernel=w.KERNEL_TMA, use_graph=0)
+            one_step[s] = time_levels(sims[s], 200) / 200
+            sims[s].set_tuning(kernel=w.KERNEL_TEMPORAL, temporal_t=saved[1], tile_h=tuned[s]["tile_h"])
+        else:
+            one_step[s] = None
 
     # end-to-end through the public API with host buffers (pinned), copies timed
     pu0 = torch.from_numpy(u0).pin_memory()
@@ -247,11 +281,26 @@ def run_ours(args, rank, world, local_rank):
         return None
 
     peak, peak_src = measured_peaks()
-    avg_launch = stepn_s / n_two_step_launches
-    alg_bytes = 12 * N * N  # read u^k, read u^{k-1}, write u^{k+1} (FP32)
-    achieved = alg_bytes / avg_launch / 1e9
     src_hash = kernel_source_hash()
-    traffic = NCU_TRAFFIC.get(src_hash)
+    per_scheme_stepn = {s: sum(a.elapsed_time(b) for ss, a, b in timing if ss == s) / 1e3 for s in SCHEMES}
+    if kernel == w.KERNEL_TEMPORAL:
+        # step_n(1999) = floor(1999/T) temporal launches + (1999 mod T) one-step launches
+        T = T13
+        n_temp = args.steps * len(SCHEMES) * ((STEPS_PER_SCHEME - 1) // T)
+        n_single = args.steps * len(SCHEMES) * ((STEPS_PER_SCHEME - 1) % T)
+        single_s = sum(args.steps * ((STEPS_PER_SCHEME - 1) % T) * (one_step[s] or 0.0) for s in SCHEMES)
+        avg_launch = (stepn_s - single_s) / n_temp
+        alg_bytes = 16 * N * N  # per launch: read u^k, u^{k-1}; write u^{k+T}, u^{k+T-1} (FP32)
+        kname = f"k3_temporal (FP32, T={T}, 9/13-point)"
+        effective = 12 * T * N * N / avg_launch / 1e9  # bytes the one-step kernels would move
+    else:
+        T = 1
+        avg_launch = stepn_s / (args.steps * len(SCHEMES) * (STEPS_PER_SCHEME - 1))
+        alg_bytes = 12 * N * N  # read u^k, read u^{k-1}, write u^{k+1} (FP32)
+        kname = "k2_tma (two-step, FP32, 9/13-point)"
+        effective = alg_bytes / avg_launch / 1e9
+    achieved = alg_bytes / avg_launch / 1e9
+    traffic = NCU_TRAFFIC.get((kname.split()[0], src_hash))
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": "G point-updates/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(elapsed / args.steps * 1e3, 3),
@@ -260,17 +309,23 @@ def run_ours(args, rank, world, local_rank):
         "config": {"workload": WORKLOAD, "grid": N, "schemes": list(SCHEMES),
                    "time_levels_per_scheme": STEPS_PER_SCHEME, "boundary": "periodic",
                    "point_updates_per_step": pts_step, "l2_flush_between_steps": True,
-                   "two_step_kernel": {1: "simple", 2: "tma"}.get(kernel, str(kernel)),
+                   "autotuned": {str(s): tuned[s] for s in SCHEMES},
                    "parallelism": f"replicas x{world}"},
-        "roofline": {"bound": "hbm", "kernel": "k2_tma (two-step, FP32, 13/9-point)",
+        "roofline": {"bound": "hbm", "kernel": kname,
                      "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "peak_source": peak_src,
-                     "algorithmic_bytes_per_launch": alg_bytes,
-                     "avg_launch_us": round(avg_launch * 1e6, 3), "traffic": traffic},
+                     "algorithmic_bytes_per_launch": alg_bytes, "levels_per_launch": T,
+                     "avg_launch_us": round(avg_launch * 1e6, 3), "traffic": traffic,
+                     "unblocked_equivalent_gbs": round(effective, 1)},
+        "per_scheme_ms_per_level": {str(s): round(per_scheme_stepn[s] / (args.steps * (STEPS_PER_SCHEME - 1)) * 1e3, 5)
+                                    for s in SCHEMES},
         "e2e": {"value": round(e2e_value, 3), "unit": "G point-updates/s",
                 "h2d_bytes_per_step": len(SCHEMES) * 2 * 8 * N * N,
                 "d2h_bytes_per_step": len(SCHEMES) * (8 * 8 + 4)},
         "gpu_launches": launches,
+        "one_step_kernel": ({"kernel": "k2_tma", "avg_launch_us": {str(s): round(one_step[s] * 1e6, 3) for s in SCHEMES},
+                             "frac": {str(s): round(12 * N * N / one_step[s] / 1e9 / peak, 4) for s in SCHEMES}}
+                            if all(one_step[s] for s in SCHEMES) else None),
         "clocks": clk.summary(),
         "result_norms": {str(s): [results[s][0], results[s][1]] for s in SCHEMES},
     }
