@@ -250,6 +250,47 @@ int wave2d_error_norms_noalloc(const void *field, int dtype, int nx, int ny, int
                                double c, double t, const wave2d_exact *ex, double *rel_l2,
                                double *rel_linf, void *stream);
 
+/* ------------------------------------------------------------------------ */
+/* Batched stepping of many independent simulations (FP32 storage, one       */
+/* boundary type and one device for the whole batch).  A run advances every  */
+/* instance by its own number of two-steps (Eq. A2) in quanta of Tq <= 4     */
+/* levels; each quantum is one launch over the tiles of all instances still  */
+/* running, the quanta of a run are replayed from one CUDA graph, and every  */
+/* instance ends bit for bit where the same steps on its own handle end.     */
+/* The handles stay owned by the caller and must outlive the batch; they may  */
+/* be stepped, checkpointed or queried individually between batch calls.     */
+/* ------------------------------------------------------------------------ */
+typedef struct wave2d_batch *wave2d_batch_t;
+
+/* Group n handles; opt (may be NULL) fixes the quantum (temporal_t, 1..4)
+ * and the tile height (tile_h, 32 or 64); zero fields keep the defaults
+ * (4 and 32) until wave2d_batch_autotune chooses.  WAVE2D_ERR_ARG for
+ * non-F32 handles, mixed boundaries or devices, or a repeated handle. */
+int wave2d_batch_create(wave2d_t *handles, int n, const wave2d_tune *opt, wave2d_batch_t *out);
+
+/* First step (Eq. A1) of every instance in one launch: u0[i], v0[i] are the
+ * nx*ny FP64 arrays of instance i, all on the host (on_device = 0) or all on
+ * the device (1).  Afterwards every instance is at k = 1. */
+int wave2d_batch_first_step(wave2d_batch_t b, const double *const *u0, const double *const *v0,
+                            int on_device);
+
+/* Advance instance i by steps[i] >= 0 levels, asynchronously on the first
+ * handle's stream.  The captured run is reused while the step counts and the
+ * handles' plane pairs repeat. */
+int wave2d_batch_run(wave2d_batch_t b, const int64_t *steps);
+
+/* Time the run for min(steps[i], probe_steps) levels with quanta 2 and 4 and
+ * tile heights 32 and 64 on a snapshot of every instance, restore every
+ * instance exactly and keep the fastest (written to *best, may be NULL). */
+int wave2d_batch_autotune(wave2d_batch_t b, const int64_t *steps, int64_t probe_steps,
+                          wave2d_tune *best);
+
+/* FP64 L2 norm sqrt(sum u^2) and max |u| of every instance's current level:
+ * out[2i], out[2i+1].  Synchronises. */
+int wave2d_batch_norms(wave2d_batch_t b, double *out);
+
+void wave2d_batch_destroy(wave2d_batch_t b);
+
 /* Number of kernels the library has launched in this process (graph
  * launches count every kernel node).  For launch accounting in benchmarks. */
 int64_t wave2d_launch_count(void);

@@ -49,41 +49,18 @@ __device__ __forceinline__ Row4 smem_row4(const float* row, int lp_i, int v_i, i
     return r;
 }
 
-template <int S, bool PER, int RVW, int OH, int T, int NW>
-__global__ void __launch_bounds__(NW * 32, 1)
-    k3_temporal(const __grid_constant__ CUtensorMap tm_cur, const __grid_constant__ CUtensorMap tm_prev,
-                float* __restrict__ out_cur, float* __restrict__ out_prev, Geo g, Coef3<float> a,
-                int tiles_x, int gw, int* status) {
-    using C = TemporalCfg<S, RVW, OH, T>;
-    constexpr int R = C::R, RW = C::RW, RH = C::RH, WPR = C::WPR, NRG = NW / WPR;
+// Advance a staged region T levels in shared memory.  Q holds level k and P
+// level k-1 on RH rows of 4*RVW floats whose column 0 is grid column gx0 and
+// row 0 grid row gy0.  Level t is computed for region vectors [t, RVW-t) and
+// rows [R t, RH - R t), in place over level t-2; the CTA synchronises after
+// every level.  On return level k+T is in (T odd ? P : Q), level k+T-1 in the
+// other buffer.  Zero boundary: nodes outside the grid are kept at zero.
+template <int S, bool PER, int RVW, int T, int NW>
+__device__ __forceinline__ void region_advance(float* Q, float* P, int RH, int gx0, int gy0, const Geo& g,
+                                               const Coef3<float>& a) {
+    constexpr int R = (S == 13) ? 2 : 1, RW = 4 * RVW, WPR = RVW / 32, NRG = NW / WPR;
     static_assert(NW % WPR == 0, "warps per row group");
-    extern __shared__ __align__(1024) unsigned char smem_raw[];
-    uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
-    float* Q = reinterpret_cast<float*>(smem_raw + 1024);  // u^k, later odd/even levels
-    float* P = Q + RW * RH;                                // u^{k-1}
-
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int tx = blockIdx.x % tiles_x, ty = blockIdx.x / tiles_x;
-    const int gx0 = tx * C::OW - 4 * T;  // grid column of region column 0
-    const int gy0 = ty * OH - C::HY;     // grid row of region row 0
-
-    if (tid == 0) {
-        mbar_init(bar, 1);
-        fence_barrier_init();
-        fence_proxy_async_smem();
-    }
-    __syncthreads();
-    if (tid == 0) {
-        mbar_arrive_expect_tx(bar, 2u * C::BUF_BYTES);
-        tma_load_2d(Q, &tm_cur, bar, g.G + gx0, g.G + gy0);
-        tma_load_2d(P, &tm_prev, bar, g.G + gx0, g.G + gy0);
-    }
-    const bool ok = mbar_wait_bounded(bar, 0, status);
-    if (!__syncthreads_and(ok)) {
-        if (tid == 0) mbar_wait_bounded(bar, 0, status);  // drain the copies before exit
-        return;
-    }
-
     const int vidx = (warp % WPR) * 32 + lane;  // region vector owned by this thread
     const int rg = warp / WPR;                  // row group
     const int v_i = 4 * vidx;
@@ -95,7 +72,6 @@ __global__ void __launch_bounds__(NW * 32, 1)
         const int gx = gx0 + v_i + e;
         colin[e] = gx >= 0 && gx < g.nx;
     }
-
 #pragma unroll 1
     for (int t = 1; t <= T; ++t) {
         const float* src = (t & 1) ? Q : P;  // level k+t-1
@@ -154,47 +130,93 @@ __global__ void __launch_bounds__(NW * 32, 1)
         }
         __syncthreads();
     }
+}
 
-    // Write u^{k+T} and u^{k+T-1} for the tile.
-    const float* lastb = (T & 1) ? P : Q;
-    const float* otherb = (T & 1) ? Q : P;
-    if (vidx >= T && vidx < RVW - T) {
-        const int gx = gx0 + v_i;
-        const bool edge = PER && (tx * C::OW < gw || tx * C::OW + C::OW > g.nx - gw || ty * OH < gw ||
-                                  ty * OH + OH > g.ny - gw);
-        const bool vec_images = (g.nx % 4 == 0) && g.nx >= 2 * gw && g.ny >= 2 * gw;
-        const int per = (OH + NRG - 1) / NRG;
-        const int r0 = C::HY + rg * per, r1 = min(r0 + per, C::HY + OH);
+// Write region rows [row0, row0 + OH) and vectors [vec0, vec0 + OWV) of the
+// last two levels to the output planes (and their periodic images in the
+// first gw rings when `edge`).
+template <bool PER, int RVW, int NW>
+__device__ __forceinline__ void region_store(const float* lastb, const float* otherb, int row0, int OH, int vec0,
+                                             int OWV, int gx0, int gy0, const Geo& g, float* out_cur,
+                                             float* out_prev, int gw, bool edge) {
+    constexpr int RW = 4 * RVW, WPR = RVW / 32, NRG = NW / WPR;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int vidx = (warp % WPR) * 32 + lane;
+    const int rg = warp / WPR;
+    const int v_i = 4 * vidx;
+    if (vidx < vec0 || vidx >= vec0 + OWV) return;
+    const int gx = gx0 + v_i;
+    const bool vec_images = (g.nx % 4 == 0) && g.nx >= 2 * gw && g.ny >= 2 * gw;
+    const int per = (OH + NRG - 1) / NRG;
+    const int r0 = row0 + rg * per, r1 = min(r0 + per, row0 + OH);
 #pragma unroll 1
-        for (int r = r0; r < r1; ++r) {
-            const int gy = gy0 + r;
-            if (gy >= g.ny || gx >= g.nx) break;
-            const float4 vc = *reinterpret_cast<const float4*>(lastb + r * RW + v_i);
-            const float4 vp = *reinterpret_cast<const float4*>(otherb + r * RW + v_i);
-            const size_t o = off(g, gx, gy);
-            if (gx + 4 <= g.nx) {
-                *reinterpret_cast<float4*>(out_cur + o) = vc;
-                *reinterpret_cast<float4*>(out_prev + o) = vp;
-                if (edge && vec_images) {
-                    store_vec_images(reinterpret_cast<float4*>(out_cur), g, gx, gy, vc, gw, 4);
-                    store_vec_images(reinterpret_cast<float4*>(out_prev), g, gx, gy, vp, gw, 4);
-                }
-            } else {
-                const float c4[4] = {vc.x, vc.y, vc.z, vc.w}, p4[4] = {vp.x, vp.y, vp.z, vp.w};
-                for (int e = 0; e < 4 && gx + e < g.nx; ++e) {
-                    out_cur[o + e] = c4[e];
-                    out_prev[o + e] = p4[e];
-                }
+    for (int r = r0; r < r1; ++r) {
+        const int gy = gy0 + r;
+        if (gy >= g.ny || gx >= g.nx) break;
+        const float4 vc = *reinterpret_cast<const float4*>(lastb + r * RW + v_i);
+        const float4 vp = *reinterpret_cast<const float4*>(otherb + r * RW + v_i);
+        const size_t o = off(g, gx, gy);
+        if (gx + 4 <= g.nx) {
+            *reinterpret_cast<float4*>(out_cur + o) = vc;
+            *reinterpret_cast<float4*>(out_prev + o) = vp;
+            if (PER && edge && vec_images) {
+                store_vec_images(reinterpret_cast<float4*>(out_cur), g, gx, gy, vc, gw, 4);
+                store_vec_images(reinterpret_cast<float4*>(out_prev), g, gx, gy, vp, gw, 4);
             }
-            if (edge && !vec_images) {
-                const Level Lc{out_cur, nullptr}, Lp{out_prev, nullptr};
-                for (int e = 0; e < 4 && gx + e < g.nx; ++e) {
-                    write_images<DT_F32>(Lc, g, gx + e, gy, out_cur[o + e], gw);
-                    write_images<DT_F32>(Lp, g, gx + e, gy, out_prev[o + e], gw);
-                }
+        } else {
+            const float c4[4] = {vc.x, vc.y, vc.z, vc.w}, p4[4] = {vp.x, vp.y, vp.z, vp.w};
+            for (int e = 0; e < 4 && gx + e < g.nx; ++e) {
+                out_cur[o + e] = c4[e];
+                out_prev[o + e] = p4[e];
+            }
+        }
+        if (PER && edge && !vec_images) {
+            const Level Lc{out_cur, nullptr}, Lp{out_prev, nullptr};
+            for (int e = 0; e < 4 && gx + e < g.nx; ++e) {
+                write_images<DT_F32>(Lc, g, gx + e, gy, out_cur[o + e], gw);
+                write_images<DT_F32>(Lp, g, gx + e, gy, out_prev[o + e], gw);
             }
         }
     }
+}
+
+template <int S, bool PER, int RVW, int OH, int T, int NW>
+__global__ void __launch_bounds__(NW * 32, 1)
+    k3_temporal(const __grid_constant__ CUtensorMap tm_cur, const __grid_constant__ CUtensorMap tm_prev,
+                float* __restrict__ out_cur, float* __restrict__ out_prev, Geo g, Coef3<float> a,
+                int tiles_x, int gw, int* status) {
+    using C = TemporalCfg<S, RVW, OH, T>;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
+    float* Q = reinterpret_cast<float*>(smem_raw + 1024);  // u^k
+    float* P = Q + C::RW * C::RH;                          // u^{k-1}
+
+    const int tid = threadIdx.x;
+    const int tx = blockIdx.x % tiles_x, ty = blockIdx.x / tiles_x;
+    const int gx0 = tx * C::OW - 4 * T;  // grid column of region column 0
+    const int gy0 = ty * OH - C::HY;     // grid row of region row 0
+
+    if (tid == 0) {
+        mbar_init(bar, 1);
+        fence_barrier_init();
+        fence_proxy_async_smem();
+    }
+    __syncthreads();
+    if (tid == 0) {
+        mbar_arrive_expect_tx(bar, 2u * C::BUF_BYTES);
+        tma_load_2d(Q, &tm_cur, bar, g.G + gx0, g.G + gy0);
+        tma_load_2d(P, &tm_prev, bar, g.G + gx0, g.G + gy0);
+    }
+    const bool ok = mbar_wait_bounded(bar, 0, status);
+    if (!__syncthreads_and(ok)) {
+        if (tid == 0) mbar_wait_bounded(bar, 0, status);  // drain the copies before exit
+        return;
+    }
+    region_advance<S, PER, RVW, T, NW>(Q, P, C::RH, gx0, gy0, g, a);
+    const bool edge = PER && (tx * C::OW < gw || tx * C::OW + C::OW > g.nx - gw || ty * OH < gw ||
+                              ty * OH + OH > g.ny - gw);
+    region_store<PER, RVW, NW>((T & 1) ? P : Q, (T & 1) ? Q : P, C::HY, OH, T, C::OWV, gx0, gy0, g, out_cur,
+                               out_prev, gw, edge);
 }
 
 // Periodic images of every node within gw of an edge, re-derived from the

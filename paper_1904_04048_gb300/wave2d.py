@@ -90,6 +90,14 @@ SIGNATURES = {
     "wave2d_last_error": (ctypes.c_char_p, []),
     "wave2d_launch_count": (ctypes.c_int64, []),
     "wave2d_lambda_max": (ctypes.c_double, [ctypes.c_int, ctypes.c_int]),
+    "wave2d_batch_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.POINTER(wave2d_tune),
+                                           ctypes.POINTER(_P)]),
+    "wave2d_batch_first_step": (ctypes.c_int, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.c_int]),
+    "wave2d_batch_run": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int64)]),
+    "wave2d_batch_autotune": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int64), ctypes.c_int64,
+                                             ctypes.POINTER(wave2d_tune)]),
+    "wave2d_batch_norms": (ctypes.c_int, [_P, _D]),
+    "wave2d_batch_destroy": (None, [_P]),
     "wave2d_error_norms_noalloc": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int64,
                                                   ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                                   ctypes.POINTER(wave2d_exact), _D, _D, _P]),
@@ -297,3 +305,67 @@ class Wave2D:
 
     def sync(self):
         check(lib().wave2d_sync(self._h))
+
+
+class Batch:
+    """A batch of handles stepped together (``wave2d_batch_t``)."""
+
+    def __init__(self, sims, temporal_t=0, tile_h=0):
+        self.sims = list(sims)
+        arr = (ctypes.c_void_p * len(self.sims))(*[s.handle.value for s in self.sims])
+        opt = wave2d_tune(KERNEL_TEMPORAL, int(tile_h), int(temporal_t), -1, 0)
+        out = ctypes.c_void_p()
+        check(lib().wave2d_batch_create(arr, len(self.sims), ctypes.byref(opt), ctypes.byref(out)))
+        self._b = out
+        self._keep = arr
+
+    def close(self):
+        if getattr(self, "_b", None):
+            lib().wave2d_batch_destroy(self._b)
+            self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def first_step(self, u0s, v0s):
+        """Host (numpy) or device (torch float64) initial data, one pair per instance."""
+        n = len(self.sims)
+        keep = []
+        on_dev = None
+        pu, pv = (ctypes.c_void_p * n)(), (ctypes.c_void_p * n)()
+        for i, (s, a, b) in enumerate(zip(self.sims, u0s, v0s)):
+            if isinstance(a, np.ndarray) or not hasattr(a, "data_ptr"):
+                a = _host_f64(a, s.nx * s.ny)
+                b = _host_f64(b, s.nx * s.ny)
+            keep += [a, b]
+            (p1, d1), (p2, d2) = _ptr(a), _ptr(b)
+            if on_dev is None:
+                on_dev = d1
+            if d1 != on_dev or d2 != on_dev:
+                raise ValueError("all initial data must be on the host or all on the device")
+            pu[i], pv[i] = p1, p2
+        check(lib().wave2d_batch_first_step(self._b, pu, pv, int(on_dev or 0)))
+
+    def run(self, steps):
+        arr = (ctypes.c_int64 * len(self.sims))(*[int(x) for x in steps])
+        check(lib().wave2d_batch_run(self._b, arr))
+
+    def autotune(self, steps, probe_steps=32) -> wave2d_tune:
+        arr = (ctypes.c_int64 * len(self.sims))(*[int(x) for x in steps])
+        best = wave2d_tune()
+        check(lib().wave2d_batch_autotune(self._b, arr, int(probe_steps), ctypes.byref(best)))
+        return best
+
+    def norms(self):
+        out = np.zeros(2 * len(self.sims))
+        check(lib().wave2d_batch_norms(self._b, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+        return out.reshape(-1, 2)
