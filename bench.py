@@ -329,9 +329,124 @@ def run_ours(args, rank, world, local_rank):
         "clocks": clk.summary(),
         "result_norms": {str(s): [results[s][0], results[s][1]] for s in SCHEMES},
     }
+    if world == 1 and not args.no_extras:
+        line["batched"] = measure_batched(w, torch)
+        line["served"] = measure_served(w, torch)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = time_oracle(u0, v0, args.cpu_budget)
     return line
+
+
+def measure_batched(w, torch):
+    """512 uneven instances (sizes log-uniform 64..1024, mixed schemes, Courant
+    numbers and 100..2000 steps, zero boundary, centred Gaussian pulse): one
+    batched run per repetition vs the plain per-grid launch loop."""
+    from initial_data import BC_ZERO, batch_instances, instance_ic
+    insts = batch_instances(512, seed=4)
+    data = [instance_ic(i) for i in insts]
+    du = [torch.from_numpy(d[0]).cuda() for d in data]
+    dv = [torch.from_numpy(d[1]).cuda() for d in data]
+    steps = [i.steps for i in insts]
+    pts = sum(i.n * i.n * (i.steps + 1) for i in insts)
+    stream = torch.cuda.Stream()
+    sims = [w.Wave2D(i.n, i.n, h, i.lam * h, scheme=i.scheme, bc=BC_ZERO, dtype=w.F32, stream=stream.cuda_stream)
+            for i, (_, _, h) in zip(insts, data)]
+    b = w.Batch(sims)
+    b.first_step(du, dv)
+    best = b.autotune(steps, probe_steps=32)
+    b.first_step(du, dv)
+    b.run(steps)            # builds and captures the run
+    torch.cuda.synchronize()
+    reps = 3
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        b.first_step(du, dv)
+        b.run(steps)
+        norms = b.norms()
+    torch.cuda.synchronize()
+    batched = (time.perf_counter() - t0) / reps
+    for sm in sims:
+        sm.set_tuning(kernel=w.KERNEL_AUTO, use_graph=0)
+    t0 = time.perf_counter()
+    for sm, a, c, n in zip(sims, du, dv, steps):
+        sm.first_step(a, c)
+        sm.step_n(n)
+    plain_norms = [sm.error_vs_exact()[0] for sm in sims]
+    torch.cuda.synchronize()
+    plain = time.perf_counter() - t0
+    agree = max(abs(x - y[0]) / y[0] for x, y in zip(plain_norms, norms))
+    b.close()
+    for sm in sims:
+        sm.close()
+    return {"workload": "512 instances, n log-uniform 64..1024 (seed 4), schemes 5/9/13, lambda U(0.3, 0.9 max), "
+                        "100..2000 steps, FP32, zero boundary, centred Gaussian pulse",
+            "node_updates": pts, "value": round(pts / batched / 1e9, 2), "unit": "G point-updates/s",
+            "ms": round(batched * 1e3, 2), "plain_loop_value": round(pts / plain / 1e9, 2),
+            "plain_loop_ms": round(plain * 1e3, 1), "speedup_vs_plain": round(plain / batched, 2),
+            "quantum": best.temporal_t, "tile_h": best.tile_h, "max_rel_norm_diff_vs_plain": agree,
+            "timing": "host wall clock around first step + run + norms to host, 3 repetitions"}
+
+
+def measure_served(w, torch):
+    """Poisson stream of 2000 requests at 200 / s (sizes log-uniform
+    128..2048, mixed schemes, Courant numbers and 100..5000 steps, FP32, zero
+    boundary, Gaussian pulse), 16 GiB budget: latency and throughput, plus
+    the same requests all at once (capacity) and sequential plain launches on
+    a sample."""
+    import numpy as np
+    from initial_data import request_stream
+    reqs = request_stream(count=2000, seed=5)
+
+    def serve(paced):
+        with w.Server(budget_bytes=16 << 30, max_resident=4096, quantum=64) as srv:
+            t0 = time.perf_counter()
+            for i, rq in enumerate(reqs):
+                if paced:
+                    d = t0 + rq.arrival_s - time.perf_counter()
+                    if d > 0:
+                        time.sleep(d)
+                n = rq.inst.n
+                h = 1.0 / (n + 1)
+                srv.submit(n, n, h, rq.inst.lam * h, rq.inst.steps, scheme=rq.inst.scheme,
+                           pulse=(1.0, 0.5, 0.5, 0.05), tag=i)
+            srv.drain(3600)
+            comps = srv.poll(max_n=len(reqs) + 8)
+            st = srv.stats()
+        lat = np.array([c.t_done - c.t_submit for c in comps])
+        wall = max(c.t_done for c in comps) - min(c.t_submit for c in comps)
+        assert len(comps) == len(reqs) and all(c.status == 0 for c in comps)
+        return lat, wall, st
+
+    pts = sum(r.inst.n ** 2 * (r.inst.steps + 1) for r in reqs)
+    lat, wall, st = serve(True)
+    _, wall_sat, _ = serve(False)
+    sample = reqs[:40]
+    t0 = time.perf_counter()
+    spts = 0
+    for rq in sample:
+        n = rq.inst.n
+        h = 1.0 / (n + 1)
+        x = (np.arange(n) + 1) * h
+        g = np.exp(-(x - 0.5) ** 2 / (2 * 0.05 ** 2))
+        u0 = np.outer(g, g)
+        with w.Wave2D(n, n, h, rq.inst.lam * h, scheme=rq.inst.scheme, dtype=w.F32) as sm:
+            sm.set_tuning(use_graph=0)
+            sm.first_step(u0, np.zeros_like(u0))
+            sm.step_n(rq.inst.steps)
+            sm.error_vs_exact()
+        spts += n * n * (rq.inst.steps + 1)
+    seq = spts / (time.perf_counter() - t0) / 1e9
+    return {"workload": "2000 Poisson requests at 200/s (seed 5), n log-uniform 128..2048, schemes 5/9/13, "
+                        "100..5000 steps, FP32, zero boundary, Gaussian pulse, 16 GiB budget, quantum 64",
+            "node_updates": pts, "offered_value": round(pts / reqs[-1].arrival_s / 1e9, 2),
+            "value": round(pts / wall / 1e9, 2), "unit": "G point-updates/s",
+            "p50_ms": round(float(np.percentile(lat, 50)) * 1e3, 2),
+            "p99_ms": round(float(np.percentile(lat, 99)) * 1e3, 2),
+            "max_resident": st.max_resident_seen, "rounds": st.rounds,
+            "saturated_value": round(pts / wall_sat / 1e9, 2),
+            "sequential_plain_value": round(seq, 2),
+            "saturated_speedup_vs_sequential_plain": round(pts / wall_sat / 1e9 / seq, 2),
+            "latency": "submission to norms on the host (library steady clock)"}
 
 
 def run_reference(args, rank):
@@ -378,6 +493,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle time for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the batched and served workloads")
     ap.add_argument("--ref-levels", type=int, default=4, help="time levels per scheme per reference step")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))

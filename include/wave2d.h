@@ -264,7 +264,9 @@ typedef struct wave2d_batch *wave2d_batch_t;
 
 /* Group n handles; opt (may be NULL) fixes the quantum (temporal_t, 1..4)
  * and the tile height (tile_h, 32 or 64); zero fields keep the defaults
- * (4 and 32) until wave2d_batch_autotune chooses.  WAVE2D_ERR_ARG for
+ * (4 and 32) until wave2d_batch_autotune chooses; use_graph = 0 launches the
+ * quanta of every run directly (for runs used once) instead of capturing a
+ * graph.  WAVE2D_ERR_ARG for
  * non-F32 handles, mixed boundaries or devices, or a repeated handle. */
 int wave2d_batch_create(wave2d_t *handles, int n, const wave2d_tune *opt, wave2d_batch_t *out);
 
@@ -290,6 +292,74 @@ int wave2d_batch_autotune(wave2d_batch_t b, const int64_t *steps, int64_t probe_
 int wave2d_batch_norms(wave2d_batch_t b, double *out);
 
 void wave2d_batch_destroy(wave2d_batch_t b);
+
+/* ------------------------------------------------------------------------ */
+/* Serving: continuous batching of independent simulations (FP32 storage,    */
+/* zero boundary).  A scheduler thread admits queued requests in arrival     */
+/* order while the device-memory budget and the slot limit allow, runs the   */
+/* first step (Eq. A1) of the newly admitted ones in one batched launch,     */
+/* advances every resident simulation by up to `quantum` two-steps (Eq. A2)  */
+/* per round in one batched run, and retires finished ones (FP64 norms to the */
+/* host, optional copy of the final level, memory released).  Requests that  */
+/* arrive while others run join at the next round.  A result does not depend  */
+/* on what else was resident (same per-node arithmetic as a single handle).  */
+/* ------------------------------------------------------------------------ */
+typedef struct wave2d_server *wave2d_server_t;
+
+typedef struct {
+    int32_t nx, ny, scheme, flags; /* flags: WAVE2D_CONVENTIONAL, WAVE2D_ALLOW_UNSTABLE        */
+    double h, tau, c;
+    int64_t steps;                 /* two-steps after the first step (levels = steps + 1)    */
+    const double *u0, *v0;         /* host FP64 nx*ny initial data (copied at submit), or     */
+                                   /* both NULL for the Gaussian pulse below                 */
+    double pulse_amp, pulse_cx, pulse_cy, pulse_sigma; /* u0 = amp exp(-|x-c|^2/(2 sigma^2)),
+                                      v0 = 0, nodes at x = ((i+1) h, (j+1) h)               */
+    double *out_field;             /* optional host buffer of nx*ny doubles that receives the
+                                      final level; must stay valid until its completion is
+                                      polled                                               */
+    uint64_t tag;                  /* returned in the completion                             */
+} wave2d_request;
+
+typedef struct {
+    uint64_t tag;
+    int32_t status;                /* WAVE2D_OK or the error of this request                */
+    int32_t reserved;
+    double l2, linf;               /* FP64 sqrt(sum u^2) and max |u| of the final level      */
+    int64_t k;                     /* index of the final level                              */
+    double t_submit, t_admit, t_done; /* library steady clock, seconds                       */
+} wave2d_completion;
+
+typedef struct {
+    int64_t submitted, completed, queued, node_updates, rounds, used_bytes;
+    int32_t max_resident_seen, reserved;
+} wave2d_server_stats_t;
+
+/* Device bytes a handle of this size and type holds (the admission cost). */
+int64_t wave2d_required_bytes(int nx, int ny, int dtype);
+
+/* Start a server on the current device.  budget_bytes: device memory that
+ * resident simulations may hold; max_resident: slot limit; quantum: two-steps
+ * per round; opt (may be NULL): temporal_t (1..4) and tile_h (32 | 64) of the
+ * batched runs; stream: cudaStream_t to use, NULL = a new one. */
+int wave2d_server_create(int64_t budget_bytes, int max_resident, int quantum, const wave2d_tune *opt,
+                         void *stream, wave2d_server_t *out);
+
+/* Queue a request (thread-safe).  Errors: WAVE2D_ERR_ARG (bad request),
+ * WAVE2D_ERR_UNSTABLE, WAVE2D_ERR_OOM (larger than the whole budget),
+ * WAVE2D_ERR_STATE (server shutting down). */
+int wave2d_server_submit(wave2d_server_t s, const wave2d_request *r);
+
+/* Move up to max completions to out (thread-safe, non-blocking). */
+int wave2d_server_poll(wave2d_server_t s, wave2d_completion *out, int max, int *n_out);
+
+/* Wait until every submitted request has completed (WAVE2D_ERR_TIMEOUT
+ * after timeout_s seconds). */
+int wave2d_server_drain(wave2d_server_t s, double timeout_s);
+
+int wave2d_server_stats(wave2d_server_t s, wave2d_server_stats_t *st);
+
+/* Finish all queued and running requests, then stop the scheduler. */
+void wave2d_server_destroy(wave2d_server_t s);
 
 /* Number of kernels the library has launched in this process (graph
  * launches count every kernel node).  For launch accounting in benchmarks. */

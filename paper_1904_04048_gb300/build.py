@@ -20,7 +20,7 @@ OBJ = os.path.join(PKG, "_objs")
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
               "-Xcompiler", "-fPIC", "-I" + os.path.join(ROOT, "include")]
 
-SOURCES = ["wave2d.cu", "noalloc.cu", "batch.cu"]
+SOURCES = ["wave2d.cu", "noalloc.cu", "batch.cu", "server.cu"]
 
 
 def _nvcc():

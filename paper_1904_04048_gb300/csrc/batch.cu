@@ -239,6 +239,11 @@ struct wave2d_batch {
     int graph_launches = 0;
     int plan_Tq = 0, plan_OH = 0;
     cudaEvent_t ev = nullptr;  // stream ordering with the members
+    bool direct = false;       // launch the quanta directly instead of capturing a graph
+    std::vector<int> plan_grids, plan_active;
+    const void* plan_insts = nullptr;
+    const int* plan_prefix = nullptr;
+    int plan_smem = 0;
 };
 
 namespace {
@@ -354,15 +359,29 @@ int build_plan(wave2d_batch* b, const int64_t* steps) {
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(batch kernel)");
     const int gw = per ? kGhost : 0;
     int* status = b->hs[0]->status;
-    cudaGraph_t graph = nullptr;
-    e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
-    if (e != cudaSuccess) return cuda_fail(e, "begin capture");
-    int launches = 0;
+    b->plan_grids.clear();
+    b->plan_active.clear();
     int active = n;
     for (int64_t q = 0; q < nq; ++q) {
         while (active > 0 && insts[active - 1].steps <= (int64_t)Tq * q) --active;
         if (active == 0) break;
-        kern<<<prefix[active], kBatchNW * 32, smem, b->stream>>>(dinsts, dprefix, active, (int)q, Tq, OH, gw, status);
+        b->plan_grids.push_back(prefix[active]);
+        b->plan_active.push_back(active);
+    }
+    b->plan_insts = dinsts;
+    b->plan_prefix = dprefix;
+    b->plan_smem = smem;
+    b->plan_steps.assign(steps, steps + n);
+    b->plan_Tq = Tq;
+    b->plan_OH = OH;
+    if (b->direct) return WAVE2D_OK;
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(e, "begin capture");
+    int launches = 0;
+    for (size_t q = 0; q < b->plan_grids.size(); ++q) {
+        kern<<<b->plan_grids[q], kBatchNW * 32, smem, b->stream>>>(dinsts, dprefix, b->plan_active[q], (int)q, Tq, OH,
+                                                                 gw, status);
         ++launches;
     }
     cudaError_t le = cudaGetLastError();
@@ -376,14 +395,27 @@ int build_plan(wave2d_batch* b, const int64_t* steps) {
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) return cuda_fail(e, "graph instantiate");
     b->graph_launches = launches;
-    b->plan_steps.assign(steps, steps + n);
-    b->plan_Tq = Tq;
-    b->plan_OH = OH;
+    return WAVE2D_OK;
+}
+
+// Launch the quanta of the current plan one by one (direct mode).
+int launch_direct(wave2d_batch* b) {
+    const bool per = b->bc == WAVE2D_BC_PERIODIC;
+    auto kern = per ? k6_batch_step<true> : k6_batch_step<false>;
+    const int gw = per ? kGhost : 0;
+    for (size_t q = 0; q < b->plan_grids.size(); ++q) {
+        kern<<<b->plan_grids[q], kBatchNW * 32, b->plan_smem, b->stream>>>(
+            (const BatchInst*)b->plan_insts, b->plan_prefix, b->plan_active[q], (int)q, b->Tq, b->OH, gw,
+            b->hs[0]->status);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(e, "batch kernel launch");
+        g_launches.fetch_add(1);
+    }
     return WAVE2D_OK;
 }
 
 bool same_plan(const wave2d_batch* b, const int64_t* steps) {
-    if (!b->graph || b->plan_Tq != b->Tq || b->plan_OH != b->OH || b->plan_steps.size() != b->hs.size()) return false;
+    if ((!b->graph && !b->direct) || !b->dev || b->plan_Tq != b->Tq || b->plan_OH != b->OH || b->plan_steps.size() != b->hs.size()) return false;
     for (size_t i = 0; i < b->hs.size(); ++i)
         if (b->plan_steps[i] != steps[i] || b->plan_start[i] != b->hs[i]->cur * 4 + b->hs[i]->prv) return false;
     return true;
@@ -399,9 +431,14 @@ int run_once(wave2d_batch* b, const int64_t* steps) {
         b->plan_start.resize(n);
         for (int i = 0; i < n; ++i) b->plan_start[i] = b->hs[i]->cur * 4 + b->hs[i]->prv;
     }
-    cudaError_t e = cudaGraphLaunch(b->graph, b->stream);
-    if (e != cudaSuccess) return cuda_fail(e, "batch graph launch");
-    g_launches.fetch_add(b->graph_launches);
+    if (b->direct) {
+        int rc = launch_direct(b);
+        if (rc != WAVE2D_OK) return rc;
+    } else {
+        cudaError_t e = cudaGraphLaunch(b->graph, b->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "batch graph launch");
+        g_launches.fetch_add(b->graph_launches);
+    }
     for (int i = 0; i < n; ++i) {
         wave2d* h = b->hs[i];
         const int64_t nq = (steps[i] + b->Tq - 1) / b->Tq;
@@ -447,6 +484,7 @@ int wave2d_batch_create(wave2d_t* handles, int n, const wave2d_tune* opt, wave2d
     b->num_sms = handles[0]->num_sms;
     if (opt && opt->temporal_t) b->Tq = opt->temporal_t;
     if (opt && opt->tile_h) b->OH = opt->tile_h;
+    b->direct = opt && opt->use_graph == 0;
     cudaError_t e = cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming);
     if (e != cudaSuccess) {
         delete b;

@@ -62,6 +62,27 @@ class wave2d_info_t(ctypes.Structure):
                 ("temporal_t", ctypes.c_int32)]
 
 
+class wave2d_request(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("scheme", ctypes.c_int32),
+                ("flags", ctypes.c_int32), ("h", ctypes.c_double), ("tau", ctypes.c_double),
+                ("c", ctypes.c_double), ("steps", ctypes.c_int64), ("u0", ctypes.c_void_p),
+                ("v0", ctypes.c_void_p), ("pulse_amp", ctypes.c_double), ("pulse_cx", ctypes.c_double),
+                ("pulse_cy", ctypes.c_double), ("pulse_sigma", ctypes.c_double),
+                ("out_field", ctypes.c_void_p), ("tag", ctypes.c_uint64)]
+
+
+class wave2d_completion(ctypes.Structure):
+    _fields_ = [("tag", ctypes.c_uint64), ("status", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("l2", ctypes.c_double), ("linf", ctypes.c_double), ("k", ctypes.c_int64),
+                ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double)]
+
+
+class wave2d_server_stats_t(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("queued", ctypes.c_int64),
+                ("node_updates", ctypes.c_int64), ("rounds", ctypes.c_int64), ("used_bytes", ctypes.c_int64),
+                ("max_resident_seen", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 
@@ -98,6 +119,15 @@ SIGNATURES = {
                                              ctypes.POINTER(wave2d_tune)]),
     "wave2d_batch_norms": (ctypes.c_int, [_P, _D]),
     "wave2d_batch_destroy": (None, [_P]),
+    "wave2d_required_bytes": (ctypes.c_int64, [ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    "wave2d_server_create": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.POINTER(wave2d_tune),
+                                            _P, ctypes.POINTER(_P)]),
+    "wave2d_server_submit": (ctypes.c_int, [_P, ctypes.POINTER(wave2d_request)]),
+    "wave2d_server_poll": (ctypes.c_int, [_P, ctypes.POINTER(wave2d_completion), ctypes.c_int,
+                                          ctypes.POINTER(ctypes.c_int)]),
+    "wave2d_server_drain": (ctypes.c_int, [_P, ctypes.c_double]),
+    "wave2d_server_stats": (ctypes.c_int, [_P, ctypes.POINTER(wave2d_server_stats_t)]),
+    "wave2d_server_destroy": (None, [_P]),
     "wave2d_error_norms_noalloc": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int64,
                                                   ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                                   ctypes.POINTER(wave2d_exact), _D, _D, _P]),
@@ -369,3 +399,69 @@ class Batch:
         out = np.zeros(2 * len(self.sims))
         check(lib().wave2d_batch_norms(self._b, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
         return out.reshape(-1, 2)
+
+
+class Server:
+    """Continuous-batching server (``wave2d_server_t``)."""
+
+    def __init__(self, budget_bytes=16 << 30, max_resident=512, quantum=64, temporal_t=0, tile_h=0, stream=None):
+        opt = wave2d_tune(KERNEL_TEMPORAL, int(tile_h), int(temporal_t), 0, 0)
+        out = ctypes.c_void_p()
+        check(lib().wave2d_server_create(int(budget_bytes), int(max_resident), int(quantum), ctypes.byref(opt),
+                                         ctypes.c_void_p(int(stream) if stream else 0), ctypes.byref(out)))
+        self._s = out
+        self._keep = {}
+
+    def submit(self, nx, ny, h, tau, steps, scheme=13, c=1.0, u0=None, v0=None, pulse=None, tag=0,
+               out_field=None, flags=0):
+        """Queue a request; pulse = (amp, cx, cy, sigma) when u0/v0 are not given;
+        out_field: numpy (ny, nx) float64 array receiving the final level."""
+        r = wave2d_request()
+        r.nx, r.ny, r.scheme, r.flags = int(nx), int(ny), int(scheme), int(flags)
+        r.h, r.tau, r.c, r.steps, r.tag = float(h), float(tau), float(c), int(steps), int(tag)
+        if u0 is not None:
+            a = _host_f64(u0, nx * ny)
+            b = _host_f64(v0, nx * ny)
+            r.u0 = a.ctypes.data_as(ctypes.c_void_p)
+            r.v0 = b.ctypes.data_as(ctypes.c_void_p)
+        elif pulse is not None:
+            r.pulse_amp, r.pulse_cx, r.pulse_cy, r.pulse_sigma = (float(x) for x in pulse)
+        if out_field is not None:
+            assert out_field.dtype == np.float64 and out_field.flags.c_contiguous and out_field.size == nx * ny
+            r.out_field = out_field.ctypes.data_as(ctypes.c_void_p)
+            self._keep[int(tag)] = out_field
+        check(lib().wave2d_server_submit(self._s, ctypes.byref(r)))
+
+    def poll(self, max_n=1024):
+        buf = (wave2d_completion * max_n)()
+        n = ctypes.c_int()
+        check(lib().wave2d_server_poll(self._s, buf, max_n, ctypes.byref(n)))
+        out = [buf[i] for i in range(n.value)]
+        for c in out:
+            self._keep.pop(int(c.tag), None)
+        return out
+
+    def drain(self, timeout_s=600.0):
+        check(lib().wave2d_server_drain(self._s, float(timeout_s)))
+
+    def stats(self) -> wave2d_server_stats_t:
+        st = wave2d_server_stats_t()
+        check(lib().wave2d_server_stats(self._s, ctypes.byref(st)))
+        return st
+
+    def close(self):
+        if getattr(self, "_s", None):
+            lib().wave2d_server_destroy(self._s)
+            self._s = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
