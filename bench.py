@@ -128,6 +128,23 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+# ------------------------------------------------------------ multi-rank
+def reduce_max(values, device):
+    """Element-wise maximum of per-rank timings over all ranks (every rank
+    runs its own replica; the slowest one bounds the whole job)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.tolist()]
+
+
+def whole_job_value(units_per_rank, world, max_elapsed_s, scale=1e9):
+    """Units processed by all ranks divided by the slowest rank's time."""
+    return world * units_per_rank / max_elapsed_s / scale
+
+
 # --------------------------------------------------------------- CPU oracle
 def time_oracle(u0, v0, budget_s: float):
     """Time the FP64 oracle (as it stands) on a bounded sample of the
@@ -268,13 +285,10 @@ def run_ours(args, rank, world, local_rank):
     barrier()
     e2e_elapsed = time.perf_counter() - t0
 
-    if world > 1:
-        t = torch.tensor([elapsed, e2e_elapsed], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        elapsed, e2e_elapsed = t.tolist()
+    elapsed, e2e_elapsed = reduce_max([elapsed, e2e_elapsed], dev)
     pts_step = len(SCHEMES) * STEPS_PER_SCHEME * N * N
-    value = world * args.steps * pts_step / elapsed / 1e9
-    e2e_value = world * e2e_steps * pts_step / e2e_elapsed / 1e9
+    value = whole_job_value(args.steps * pts_step, world, elapsed)
+    e2e_value = whole_job_value(e2e_steps * pts_step, world, e2e_elapsed)
     for s in SCHEMES:
         sims[s].close()
     if rank != 0:
