@@ -6,7 +6,9 @@ On a periodic grid every stencil sum of Eq. notations2 maps a Fourier mode
 onto itself.  With theta = (k1 h, k2 h) the delta sums have the symbols
     delta(1,0) -> 2 cos th1 + 2 cos th2 - 4
     delta(1,1) -> 4 cos th1 cos th2 - 4
-    delta(2,0) -> 2 cos 2th1 + 2 cos 2th2 - 4,
+    delta(2,0) -> 2 cos 2th1 + 2 cos 2th2 - 4
+(evaluated below in the equivalent half-angle forms, free of cancellation
+for long waves),
 so Lambda_a = a10 delta(1,0) + a11 delta(1,1) + a20 delta(2,0) has the symbol
 S_a (likewise S_b with the b coefficients of the first step).  Writing
 u^n = A_n cos(k.x) + B_n sin(k.x):
@@ -14,7 +16,7 @@ u^n = A_n cos(k.x) + B_n sin(k.x):
   (A_1, B_1) = (1 + S_a/2)(A_0, B_0) + tau (1 + S_b)(C_0, D_0) for
   v^0 = C_0 cos + D_0 sin;
 * the two-step (Eq. A2) gives X_{n+1} = (2 + S_a) X_n - X_{n-1}, whose
-  solution with cos(phi) = 1 + S_a/2 is
+  solution with cos(phi) = 1 + S_a/2, i.e. sin(phi/2) = sqrt(-S_a/4), is
   X_n = X_0 cos(n phi) + (X_1 - X_0 cos phi) sin(n phi) / sin(phi).
 The coefficients are the printed Section 6 ones, written here independently
 of the C oracle.  The result is exact up to rounding at any grid size, which
@@ -45,18 +47,25 @@ def section6_coeffs(scheme: int, lam: float, conventional: bool = False):
 
 
 def symbol(coef, th1: float, th2: float) -> float:
-    c1, c2 = math.cos(th1), math.cos(th2)
-    return (coef[0] * (2 * c1 + 2 * c2 - 4) + coef[1] * (4 * c1 * c2 - 4)
-            + coef[2] * (2 * math.cos(2 * th1) + 2 * math.cos(2 * th2) - 4))
+    """Symbol of a10 delta(1,0) + a11 delta(1,1) + a20 delta(2,0), written with
+    2 cos(x) - 2 = -4 sin^2(x/2) so that long waves (theta -> 0) lose no
+    digits to cancellation:
+        delta(1,0) -> -4 (sin^2(th1/2) + sin^2(th2/2))
+        delta(1,1) -> -4 (sin^2((th1+th2)/2) + sin^2((th1-th2)/2))
+        delta(2,0) -> -4 (sin^2(th1) + sin^2(th2))."""
+    s2 = lambda x: math.sin(x) ** 2
+    d10 = -4.0 * (s2(th1 / 2) + s2(th2 / 2))
+    d11 = -4.0 * (s2((th1 + th2) / 2) + s2((th1 - th2) / 2))
+    d20 = -4.0 * (s2(th1) + s2(th2))
+    return coef[0] * d10 + coef[1] * d11 + coef[2] * d20
 
 
 def _chebyshev_ratio(n: int, phi: float, cphi: float) -> float:
     """sin(n phi) / sin(phi), continuous at sin(phi) = 0."""
     s = math.sin(phi)
-    if abs(s) < 1e-7:
-        # U_{n-1}(cos phi) near phi = 0 or pi
-        sign = 1.0 if cphi > 0 else (-1.0) ** (n - 1)
-        return sign * n
+    if s == 0.0:
+        # U_{n-1}(+-1)
+        return float(n) if cphi > 0 else (-1.0) ** (n - 1) * n
     return math.sin(n * phi) / s
 
 
@@ -78,9 +87,11 @@ def amplitudes(scheme, lam, tau, k1, k2, h, n, a0=1.0, b0=0.0, c0=0.0, d0=None, 
     if n == 1:
         return A1, B1
     cphi = 1 + sa / 2
-    if abs(cphi) > 1.0:
+    if sa > 0 or sa < -4:
         raise ValueError("mode is outside the stability region")
-    phi = math.acos(cphi)
+    # cos(phi) = 1 + S/2 = 1 - 2 sin^2(phi/2): take phi from sin(phi/2), which
+    # stays well conditioned when phi is small
+    phi = 2.0 * math.asin(math.sqrt(-sa / 4.0))
     r = _chebyshev_ratio(n, phi, cphi)
     cn = math.cos(n * phi)
     return a0 * cn + (A1 - a0 * cphi) * r, b0 * cn + (B1 - b0 * cphi) * r
