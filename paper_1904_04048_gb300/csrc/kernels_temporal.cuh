@@ -72,6 +72,7 @@ __device__ __forceinline__ void region_advance(float* Q, float* P, int RH, int g
         const int gx = gx0 + v_i + e;
         colin[e] = gx >= 0 && gx < g.nx;
     }
+    const f2x a10x2 = pk2(a.a10, a.a10), a11x2 = pk2(a.a11, a.a11), a20x2 = pk2(a.a20, a.a20);
 #pragma unroll 1
     for (int t = 1; t <= T; ++t) {
         const float* src = (t & 1) ? Q : P;  // level k+t-1
@@ -93,31 +94,12 @@ __device__ __forceinline__ void region_advance(float* Q, float* P, int RH, int g
                 const float4 pv4 = *reinterpret_cast<const float4*>(dp);
                 const float pv[4] = {pv4.x, pv4.y, pv4.z, pv4.w};
                 float out[4];
+                const float* up2 = (S == 13) ? win[R + 2 < 2 * R + 1 ? R + 2 : 2 * R].a : win[R].a;
+                const float* dn2 = (S == 13) ? win[R - 2 >= 0 ? R - 2 : 0].a : win[R].a;
 #pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    Nbr<float> u;
-                    const Row4& c = win[R];
-                    const Row4& up = win[R + 1];
-                    const Row4& dn = win[R - 1];
-                    u.c = c.a[e + 2];
-                    u.e = c.a[e + 3];
-                    u.w = c.a[e + 1];
-                    u.n = up.a[e + 2];
-                    u.s = dn.a[e + 2];
-                    if constexpr (S >= 9) {
-                        u.ne = up.a[e + 3];
-                        u.nw = up.a[e + 1];
-                        u.se = dn.a[e + 3];
-                        u.sw = dn.a[e + 1];
-                    }
-                    if constexpr (S == 13) {
-                        u.ee = c.a[e + 4];
-                        u.ww = c.a[e];
-                        u.nn = win[R + 2].a[e + 2];
-                        u.ss = win[R - 2].a[e + 2];
-                    }
-                    out[e] = two_step_update<S>(u, pv[e], a);
-                }
+                for (int e = 0; e < 4; e += 2)
+                    two_step_update_pair<S>(win[R].a, win[R + 1].a, win[R - 1].a, up2, dn2, e, pv[e], pv[e + 1],
+                                            a10x2, a11x2, a20x2, out[e], out[e + 1]);
                 if constexpr (!PER) {
                     const int gy = gy0 + r;
                     const bool rowin = gy >= 0 && gy < g.ny;

@@ -1,0 +1,52 @@
+"""Precision modes over long runs (BASELINE accuracy sweep, small grid):
+FP64, FP32 and FP32x2 (double-float) storage against the closed-form
+discrete solution of a periodic plane wave after 10^4 steps.
+
+Tolerances are the measured errors of the 512^2 sweep with a margin of
+about 4x: FP64 and FP32x2 keep about 1e-10 (the two agree: double-float
+storage and arithmetic carry ~48 bits), FP32 storage drifts to ~1e-4 at
+10^4 steps (each level is rounded to 24 bits; the two-step recursion adds
+these roundings up, fastest for long waves)."""
+import math
+
+import numpy as np
+import pytest
+
+from initial_data import BC_PERIODIC, LAMBDA_MAX, plane_wave_ic
+
+pytestmark = pytest.mark.gpu
+
+TOL_1E4 = {0: 5e-10, 1: 4e-4, 2: 5e-10}
+STEPS = 10000
+N = 512
+
+
+@pytest.fixture(scope="module")
+def w():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1904_04048_gb300 import build
+    build.build()
+    from paper_1904_04048_gb300 import wave2d
+    return wave2d
+
+
+@pytest.mark.parametrize("scheme", [5, 9, 13])
+@pytest.mark.parametrize("m", [(3, 4), (16, 8)])
+@pytest.mark.parametrize("dtype", [0, 1, 2], ids=["f64", "f32", "f32x2"])
+def test_long_run_error_per_dtype(w, scheme, m, dtype):
+    from oracle import plane_wave
+    h = 1.0 / N
+    lam = 0.9 * LAMBDA_MAX[scheme]
+    tau = lam * h
+    k1, k2 = 2 * math.pi * m[0], 2 * math.pi * m[1]
+    u0, v0 = plane_wave_ic(N, N, h, k1, k2, BC_PERIODIC)
+    with w.Wave2D(N, N, h, tau, scheme=scheme, bc=BC_PERIODIC, dtype=dtype) as sim:
+        sim.first_step(u0, v0)
+        sim.step_n(STEPS)
+        _, uc, k = sim.get_state()
+    ref = plane_wave.field(scheme, lam, tau, k1, k2, h, N, N, k)
+    l2 = float(np.linalg.norm(uc - ref) / np.linalg.norm(ref))
+    linf = float(np.max(np.abs(uc - ref)) / np.max(np.abs(ref)))
+    assert l2 < TOL_1E4[dtype] and linf < TOL_1E4[dtype], (l2, linf)
