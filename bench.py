@@ -46,7 +46,7 @@ WORKLOAD = ("9-point + 13-point schemes, FP32 storage, 4096^2 periodic grid, lam
 # from an ncu capture of the same kernel source (see the profiles directory),
 # keyed by (kernel, hash of the kernel sources) so that a figure is dropped
 # once the kernel changes.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {("k3_temporal", "cc4f49c1d586fa22"): 224894976}
 
 
 def kernel_source_hash() -> str:
@@ -196,7 +196,11 @@ def run_ours(args, rank, world, local_rank):
     tuned = {}
     for s in SCHEMES:
         sims[s].first_step(du0, dv0)
-        best = sims[s].autotune(steps=64)
+        if args.fixed_tuning:  # the autotuner's choice on the measured runs
+            sims[s].set_tuning(kernel=w.KERNEL_TEMPORAL, temporal_t=4, tile_h=32)
+            best = w.wave2d_tune(w.KERNEL_TEMPORAL, 32, 4, -1, 0)
+        else:
+            best = sims[s].autotune(steps=64)
         tuned[s] = {"kernel": {1: "simple", 2: "tma", 3: "temporal"}[best.kernel],
                     "temporal_t": best.temporal_t, "tile_h": best.tile_h, "ctas_per_sm": best.ctas_per_sm}
     kernel = sims[13].info().kernel
@@ -344,6 +348,7 @@ def run_ours(args, rank, world, local_rank):
         "result_norms": {str(s): [results[s][0], results[s][1]] for s in SCHEMES},
     }
     if world == 1 and not args.no_extras:
+        line["config1"] = measure_config1(w, torch)
         line["batched"] = measure_batched(w, torch)
         line["served"] = measure_served(w, torch)
     if world == 1 and not args.no_cpu_baseline:
@@ -463,6 +468,39 @@ def measure_served(w, torch):
             "latency": "submission to norms on the host (library steady clock)"}
 
 
+def measure_config1(w, torch):
+    """5-point scheme, FP64, 256^2, h = 1/256, c = 1, lambda = 0.5, 200 time
+    levels, centred Gaussian pulse (sigma 0.05), v0 = 0, zero boundary: wall
+    time of one whole run (first step, 199 two-steps in a CUDA graph, FP64
+    norm to the host)."""
+    import numpy as np
+    from initial_data import BC_ZERO, gaussian_pulse
+    n, h, lam = 256, 1.0 / 256, 0.5
+    u0 = gaussian_pulse(n, n, h, BC_ZERO, sigma=0.05)
+    du = torch.from_numpy(u0).cuda()
+    dv = torch.zeros_like(du)
+    stream = torch.cuda.Stream()
+    with w.Wave2D(n, n, h, lam * h, scheme=5, bc=BC_ZERO, dtype=w.F64, stream=stream.cuda_stream) as sim:
+        sim.first_step(du, dv)
+        best = sim.autotune(steps=64)
+        for _ in range(3):
+            sim.first_step(du, dv)
+            sim.step_n(199)
+            sim.error_vs_exact()
+        torch.cuda.synchronize()
+        reps = 50
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            sim.first_step(du, dv)
+            sim.step_n(199)
+            l2, linf, _ = sim.error_vs_exact()
+        dt = (time.perf_counter() - t0) / reps
+    return {"workload": "5-point, FP64, 256^2, h = 1/256, lambda = 0.5, 200 levels, centred Gaussian, zero boundary",
+            "us_per_run": round(dt * 1e6, 1), "value": round(n * n * 200 / dt / 1e9, 3), "unit": "G point-updates/s",
+            "kernel": {1: "simple", 2: "tma", 3: "temporal"}.get(best.kernel), "field_l2": l2,
+            "timing": "host wall clock per run incl. norm to host, 50 runs"}
+
+
 def run_reference(args, rank):
     """The FP64 CPU oracle, as it stands, on the host cores."""
     if rank != 0:
@@ -508,6 +546,8 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle time for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the batched and served workloads")
+    ap.add_argument("--fixed-tuning", action="store_true",
+                    help="skip the autotuner (temporal kernel, T = 4, 32-row tiles), e.g. under a profiler")
     ap.add_argument("--ref-levels", type=int, default=4, help="time levels per scheme per reference step")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
