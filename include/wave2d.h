@@ -221,6 +221,14 @@ int wave2d_set_tuning(wave2d_t h, const wave2d_tune *tune);
 int wave2d_autotune(wave2d_t h, int64_t steps, wave2d_tune *best);
 int wave2d_get_info(wave2d_t h, wave2d_info_t *info);
 int wave2d_sync(wave2d_t h);
+
+/* Failure-detection self-test: launch, on the handle's stream, a kernel that
+ * waits on an mbarrier nothing ever completes, through the same bounded wait
+ * every pipelined kernel uses, with a limit of limit_cycles SM clocks
+ * (1 .. 2^31).  The wait gives up and raises the handle's timeout status,
+ * which the next synchronising call (wave2d_sync, norms, state) reports as
+ * WAVE2D_ERR_TIMEOUT and clears; the GPU stays usable. */
+int wave2d_selftest_timeout(wave2d_t h, int64_t limit_cycles);
 void wave2d_destroy(wave2d_t h);
 const char *wave2d_last_error(void);
 

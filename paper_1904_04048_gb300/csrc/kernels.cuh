@@ -441,12 +441,13 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* tm, ui
 // Spin on an mbarrier phase with a deadline: ~2^31 SM clocks (about a second
 // at the GB300 clocks).  Returns false and raises STATUS_TIMEOUT on expiry.
 constexpr long long kWaitLimitCycles = 1LL << 31;
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity, int* status) {
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity, int* status,
+                                                  long long limit = kWaitLimitCycles) {
     if (mbar_test_wait(bar, parity)) return true;
     const long long t0 = clock64();
     unsigned ns = 16;
     while (!mbar_test_wait(bar, parity)) {
-        if (clock64() - t0 > kWaitLimitCycles) {
+        if (clock64() - t0 > limit) {
             atomicOr(status, STATUS_TIMEOUT);
             return false;
         }

@@ -94,12 +94,25 @@ __device__ __forceinline__ void region_advance(float* Q, float* P, int RH, int g
                 const float4 pv4 = *reinterpret_cast<const float4*>(dp);
                 const float pv[4] = {pv4.x, pv4.y, pv4.z, pv4.w};
                 float out[4];
-                const float* up2 = (S == 13) ? win[R + 2 < 2 * R + 1 ? R + 2 : 2 * R].a : win[R].a;
-                const float* dn2 = (S == 13) ? win[R - 2 >= 0 ? R - 2 : 0].a : win[R].a;
+                if constexpr (S == 5) {
 #pragma unroll
-                for (int e = 0; e < 4; e += 2)
-                    two_step_update_pair<S>(win[R].a, win[R + 1].a, win[R - 1].a, up2, dn2, e, pv[e], pv[e + 1],
-                                            a10x2, a11x2, a20x2, out[e], out[e + 1]);
+                    for (int e = 0; e < 4; ++e) {
+                        Nbr<float> u;
+                        u.c = win[R].a[e + 2];
+                        u.e = win[R].a[e + 3];
+                        u.w = win[R].a[e + 1];
+                        u.n = win[R + 1].a[e + 2];
+                        u.s = win[R - 1].a[e + 2];
+                        out[e] = two_step_update<S>(u, pv[e], a);
+                    }
+                } else {
+                    const float* up2 = win[R + 2 < 2 * R + 1 ? R + 2 : 2 * R].a;
+                    const float* dn2 = win[R - 2 >= 0 ? R - 2 : 0].a;
+#pragma unroll
+                    for (int e = 0; e < 4; e += 2)
+                        two_step_update_pair<S>(win[R].a, win[R + 1].a, win[R - 1].a, up2, dn2, e, pv[e],
+                                                pv[e + 1], a10x2, a11x2, a20x2, out[e], out[e + 1]);
+                }
                 if constexpr (!PER) {
                     const int gy = gy0 + r;
                     const bool rowin = gy >= 0 && gy < g.ny;

@@ -111,28 +111,17 @@ __device__ __forceinline__ V lambda_sum(const Nbr<V>& u, const Coef3<V>& a) {
     return L;
 }
 
-// Two-step (Eq. A2): u^{k+1} = (2 u^k - u^{k-1}) + Lambda_a(u^k), evaluated as
-// a chain of fused multiply-adds onto the base 2 u^k - u^{k-1}:
-//   acc = 2c - p;  acc = fma(a10, delta(1,0), acc);  [acc = fma(a11, delta(1,1), acc);
-//   acc = fma(a20, delta(2,0), acc)]
-// No rounded product ever feeds an addition, so no compiler can fuse the
-// arithmetic differently from one kernel to another (the products by -4 and
-// 2 are exact).
+// Two-step (Eq. A2): u^{k+1} = (2 u^k - u^{k-1}) + Lambda_a(u^k), with
+// Lambda_a accumulated on its own (its magnitude is far below that of u for
+// smooth fields) and added to 2u^k - u^{k-1} by a single rounding.  Adding
+// each coefficient's term to the base in turn (a chain of FMAs onto
+// 2u^k - u^{k-1}) was measured to let FP32 rounding drift up to 48 times
+// faster over 10^4 steps for long waves, so this order is kept.
 template <int S, typename V>
 __device__ __forceinline__ V two_step_update(const Nbr<V>& u, V prev, const Coef3<V>& a) {
-    const V base = vsub(vscale(u.c, 2.0f), prev);
-    const V m4c = vscale(u.c, -4.0f);
-    const V d10 = vadd(vadd(vadd(u.e, u.w), vadd(u.n, u.s)), m4c);
-    V acc = vfma(a.a10, d10, base);
-    if constexpr (S >= 9) {
-        const V d11 = vadd(vadd(vadd(u.ne, u.sw), vadd(u.nw, u.se)), m4c);
-        acc = vfma(a.a11, d11, acc);
-    }
-    if constexpr (S == 13) {
-        const V d20 = vadd(vadd(vadd(u.ee, u.ww), vadd(u.nn, u.ss)), m4c);
-        acc = vfma(a.a20, d20, acc);
-    }
-    return acc;
+    V L = lambda_sum<S>(u, a);
+    V base = vsub(vscale(u.c, 2.0f), prev);
+    return vadd(base, L);
 }
 
 // First step (Eq. A1), always in FP64:
@@ -181,31 +170,36 @@ __device__ __forceinline__ f2x fma2(f2x a, f2x b, f2x c) {
 // Rows hold x-2 .. x+5 of one 4-node vector (a[k] = column x + k - 2); the
 // pair starts at node e (0 or 2).  up/dn are rows j+1 / j-1, up2/dn2 rows
 // j+2 / j-2 (13-point only).  Coefficients arrive as duplicated pairs.
+// Packed pair for the 9- and 13-point schemes.  The final addition consumes
+// the result of an FMA (a11 or a20 term), which no compiler can merge into the
+// product before it, so every lane rounds exactly as two_step_update does.
+// (For the 5-point scheme the last product would feed the addition directly,
+// and a packed multiply followed by a packed add may be fused: that scheme
+// uses the scalar path.)
 template <int S>
 __device__ __forceinline__ void two_step_update_pair(const float* c, const float* up, const float* dn,
                                                      const float* up2, const float* dn2, int e, float p0,
                                                      float p1, f2x a10, f2x a11, f2x a20, float& o0,
                                                      float& o1) {
+    static_assert(S == 9 || S == 13, "packed pair path is for the 9- and 13-point schemes");
     const f2x cc = pk2(c[e + 2], c[e + 3]);
-    const f2x base = fma2(pk2(p0, p1), pk2(-1.0f, -1.0f), mul2(cc, pk2(2.0f, 2.0f)));
     const f2x m4c = mul2(cc, pk2(-4.0f, -4.0f));
     const f2x d10 = add2(add2(add2(pk2(c[e + 3], c[e + 4]), pk2(c[e + 1], c[e + 2])),
                               add2(pk2(up[e + 2], up[e + 3]), pk2(dn[e + 2], dn[e + 3]))),
                          m4c);
-    f2x acc = fma2(a10, d10, base);
-    if constexpr (S >= 9) {
-        const f2x d11 = add2(add2(add2(pk2(up[e + 3], up[e + 4]), pk2(dn[e + 1], dn[e + 2])),
-                                  add2(pk2(up[e + 1], up[e + 2]), pk2(dn[e + 3], dn[e + 4]))),
-                             m4c);
-        acc = fma2(a11, d11, acc);
-    }
+    f2x L = mul2(a10, d10);
+    const f2x d11 = add2(add2(add2(pk2(up[e + 3], up[e + 4]), pk2(dn[e + 1], dn[e + 2])),
+                              add2(pk2(up[e + 1], up[e + 2]), pk2(dn[e + 3], dn[e + 4]))),
+                         m4c);
+    L = fma2(a11, d11, L);
     if constexpr (S == 13) {
         const f2x d20 = add2(add2(add2(pk2(c[e + 4], c[e + 5]), pk2(c[e], c[e + 1])),
                                   add2(pk2(up2[e + 2], up2[e + 3]), pk2(dn2[e + 2], dn2[e + 3]))),
                              m4c);
-        acc = fma2(a20, d20, acc);
+        L = fma2(a20, d20, L);
     }
-    upk2(acc, o0, o1);
+    const f2x base = fma2(pk2(p0, p1), pk2(-1.0f, -1.0f), mul2(cc, pk2(2.0f, 2.0f)));
+    upk2(add2(base, L), o0, o1);
 }
 
 }  // namespace w2d

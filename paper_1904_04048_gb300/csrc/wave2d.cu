@@ -595,6 +595,19 @@ static int check_status(wave2d* h) {
     return WAVE2D_OK;
 }
 
+// Self-test of the bounded wait: an mbarrier that nothing ever completes is
+// waited on with a short limit; the wait gives up, raises STATUS_TIMEOUT and
+// the kernel returns.  No copy is in flight, so nothing needs draining.
+__global__ void k_selftest_wait(int* status, long long limit) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_barrier_init();
+    }
+    __syncthreads();
+    mbar_wait_bounded(&bar, 0, status, limit);
+}
+
 }  // namespace w2d
 
 using namespace w2d;
@@ -1097,6 +1110,15 @@ int wave2d_autotune(wave2d_t h, int64_t steps, wave2d_tune* best) {
     if (rc == WAVE2D_OK) rc = check_status(h);
     if (best) *best = chosen;
     return rc;
+}
+
+int wave2d_selftest_timeout(wave2d_t h, int64_t limit_cycles) {
+    if (!h) return set_error(WAVE2D_ERR_ARG, "null handle");
+    if (limit_cycles < 1 || limit_cycles > (1LL << 31))
+        return set_error(WAVE2D_ERR_ARG, "limit must be 1 .. 2^31 cycles");
+    k_selftest_wait<<<1, 32, 0, h->stream>>>(h->status, (long long)limit_cycles);
+    W2D_LAUNCHED("self-test kernel launch");
+    return WAVE2D_OK;
 }
 
 int wave2d_sync(wave2d_t h) {

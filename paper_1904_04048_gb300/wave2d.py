@@ -107,6 +107,7 @@ SIGNATURES = {
     "wave2d_autotune": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.POINTER(wave2d_tune)]),
     "wave2d_get_info": (ctypes.c_int, [_P, ctypes.POINTER(wave2d_info_t)]),
     "wave2d_sync": (ctypes.c_int, [_P]),
+    "wave2d_selftest_timeout": (ctypes.c_int, [_P, ctypes.c_int64]),
     "wave2d_destroy": (None, [_P]),
     "wave2d_last_error": (ctypes.c_char_p, []),
     "wave2d_launch_count": (ctypes.c_int64, []),
@@ -335,6 +336,9 @@ class Wave2D:
 
     def sync(self):
         check(lib().wave2d_sync(self._h))
+
+    def selftest_timeout(self, limit_cycles=1 << 20):
+        check(lib().wave2d_selftest_timeout(self._h, int(limit_cycles)))
 
 
 class Batch:

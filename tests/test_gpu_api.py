@@ -170,3 +170,21 @@ def test_launch_counter_counts_kernels(w):
         c0 = w.launch_count()
         sim.step_n(17)
         assert w.launch_count() - c0 == 17
+
+
+def test_bounded_wait_times_out_and_reports(w):
+    """A wait that nothing completes gives up after its limit; the host reads
+    WAVE2D_ERR_TIMEOUT at the next synchronising call, the status is cleared
+    and the handle keeps working."""
+    n = 64
+    u0, v0, h = smooth_ic(n, n, BC_PERIODIC, seed=3)
+    with w.Wave2D(n, n, h, 0.5 * h, scheme=13, bc=BC_PERIODIC, dtype=w.F32) as sim:
+        sim.first_step(u0, v0)
+        sim.selftest_timeout(1 << 20)  # about 0.5 ms of SM clocks
+        with pytest.raises(w.Wave2DError) as e:
+            sim.sync()
+        assert e.value.code == w.ERR_TIMEOUT
+        sim.sync()  # cleared
+        sim.step_n(5)
+        _, uc, k = sim.get_state()
+        assert k == 6 and np.all(np.isfinite(uc))
