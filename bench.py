@@ -501,6 +501,31 @@ def measure_config1(w, torch):
             "timing": "host wall clock per run incl. norm to host, 50 runs"}
 
 
+def profile_case(kernel: str, scheme: int):
+    """A short run of one kernel at the benchmark size, for profiler captures:
+    the first step, then a few launches of the named kernel on the
+    benchmark's inputs (no timing, no JSON line).  4096^2 FP32 holds about
+    0.5 GB on the device.
+      k2_tma:      4 one-step launches (the first step comes before them)
+      k3_temporal: 3 launches of T = 4 levels, 32-row tiles"""
+    from initial_data import BC_PERIODIC, LAMBDA_MAX, pulses_and_noise
+    from paper_1904_04048_gb300 import wave2d as w
+    u0, v0 = pulses_and_noise(N, seed=SEED)
+    h = 1.0 / N
+    lam = 0.9 * LAMBDA_MAX[scheme]
+    with w.Wave2D(N, N, h, lam * h, scheme=scheme, bc=BC_PERIODIC, dtype=w.F32) as sim:
+        if kernel == "k2_tma":
+            sim.set_tuning(kernel=w.KERNEL_TMA, use_graph=0)
+            levels = 4
+        else:
+            sim.set_tuning(kernel=w.KERNEL_TEMPORAL, temporal_t=4, tile_h=32, use_graph=0)
+            levels = 12
+        sim.first_step(u0, v0)
+        sim.step_n(levels)
+        sim.sync()
+        print(f"profile case {kernel}, {scheme}-point, {N}^2: {levels} levels after the first step")
+
+
 def run_reference(args, rank):
     """The FP64 CPU oracle, as it stands, on the host cores."""
     if rank != 0:
@@ -549,7 +574,13 @@ def main():
     ap.add_argument("--fixed-tuning", action="store_true",
                     help="skip the autotuner (temporal kernel, T = 4, 32-row tiles), e.g. under a profiler")
     ap.add_argument("--ref-levels", type=int, default=4, help="time levels per scheme per reference step")
+    ap.add_argument("--profile-case", choices=["k2_tma", "k3_temporal"],
+                    help="run a short case of one kernel for a profiler capture and exit")
+    ap.add_argument("--profile-scheme", type=int, choices=[5, 9, 13], default=13)
     args = ap.parse_args()
+    if args.profile_case:
+        profile_case(args.profile_case, args.profile_scheme)
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

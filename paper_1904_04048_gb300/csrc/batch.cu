@@ -505,6 +505,7 @@ void wave2d_batch_destroy(wave2d_batch_t b) {
 static int batch_first_step_impl(wave2d_batch_t b, const double* const* u0, const double* const* v0, int on_device);
 
 int wave2d_batch_first_step(wave2d_batch_t b, const double* const* u0, const double* const* v0, int on_device) {
+    NvtxRange nvtx_range("wave2d_batch_first_step");
     if (!b || !u0 || !v0) return set_error(WAVE2D_ERR_ARG, "null argument");
     int rc = order_streams(b, true);
     if (rc == WAVE2D_OK) rc = batch_first_step_impl(b, u0, v0, on_device);
@@ -589,6 +590,7 @@ static int batch_first_step_impl(wave2d_batch_t b, const double* const* u0, cons
 static int batch_run_impl(wave2d_batch_t b, const int64_t* steps);
 
 int wave2d_batch_run(wave2d_batch_t b, const int64_t* steps) {
+    NvtxRange nvtx_range("wave2d_batch_run");
     if (!b || !steps) return set_error(WAVE2D_ERR_ARG, "null argument");
     int rc = order_streams(b, true);
     if (rc == WAVE2D_OK) rc = batch_run_impl(b, steps);
@@ -626,6 +628,7 @@ static int batch_run_impl(wave2d_batch_t b, const int64_t* steps) {
 static int batch_autotune_impl(wave2d_batch_t b, const int64_t* steps, int64_t probe_steps, wave2d_tune* best);
 
 int wave2d_batch_autotune(wave2d_batch_t b, const int64_t* steps, int64_t probe_steps, wave2d_tune* best) {
+    NvtxRange nvtx_range("wave2d_batch_autotune");
     if (!b || !steps) return set_error(WAVE2D_ERR_ARG, "null argument");
     int rc = order_streams(b, true);
     if (rc == WAVE2D_OK) rc = batch_autotune_impl(b, steps, probe_steps, best);
@@ -714,6 +717,7 @@ static int batch_autotune_impl(wave2d_batch_t b, const int64_t* steps, int64_t p
 static int batch_norms_impl(wave2d_batch_t b, double* out);
 
 int wave2d_batch_norms(wave2d_batch_t b, double* out) {
+    NvtxRange nvtx_range("wave2d_batch_norms");
     if (!b || !out) return set_error(WAVE2D_ERR_ARG, "null argument");
     int rc = order_streams(b, true);
     if (rc == WAVE2D_OK) rc = batch_norms_impl(b, out);

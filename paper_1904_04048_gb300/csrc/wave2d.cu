@@ -645,6 +645,7 @@ static void release_handle(wave2d* h) {
 }
 
 int wave2d_create(const wave2d_grid* grid, double hh, double tau, double c, int scheme, wave2d_t* out) {
+    NvtxRange nvtx_range("wave2d_create");
     if (!grid || !out) return set_error(WAVE2D_ERR_ARG, "null argument");
     *out = nullptr;
     if (scheme != 5 && scheme != 9 && scheme != 13)
@@ -816,6 +817,7 @@ int wave2d_track_error(wave2d_t h, const wave2d_exact* ex) {
 }
 
 int wave2d_first_step(wave2d_t h, const double* u0, const double* v0, int on_device) {
+    NvtxRange nvtx_range("wave2d_first_step");
     if (!h || !u0 || !v0) return set_error(WAVE2D_ERR_ARG, "null argument");
     const size_t n = (size_t)h->nx * h->ny;
     const double* du0 = u0;
@@ -843,6 +845,7 @@ int wave2d_first_step(wave2d_t h, const double* u0, const double* v0, int on_dev
 }
 
 int wave2d_step_n(wave2d_t h, int64_t n) {
+    NvtxRange nvtx_range("wave2d_step_n");
     if (!h) return set_error(WAVE2D_ERR_ARG, "null handle");
     if (n < 0) return set_error(WAVE2D_ERR_ARG, "negative step count");
     if (!h->initialized) return set_error(WAVE2D_ERR_STATE, "step_n before first_step or set_state");
@@ -869,6 +872,7 @@ int wave2d_step_n(wave2d_t h, int64_t n) {
 
 int wave2d_error_vs_exact(wave2d_t h, const wave2d_exact* ex, double* rel_l2, double* rel_linf,
                           double* spacetime_E) {
+    NvtxRange nvtx_range("wave2d_error_vs_exact");
     if (!h) return set_error(WAVE2D_ERR_ARG, "null handle");
     if (!h->initialized) return set_error(WAVE2D_ERR_STATE, "no time level computed yet");
     wave2d_exact none{};
@@ -909,6 +913,7 @@ int wave2d_error_vs_exact(wave2d_t h, const wave2d_exact* ex, double* rel_l2, do
 }
 
 int wave2d_get_state(wave2d_t h, double* u_prev, double* u_cur, int64_t* k) {
+    NvtxRange nvtx_range("wave2d_get_state");
     if (!h) return set_error(WAVE2D_ERR_ARG, "null handle");
     if (!h->initialized) return set_error(WAVE2D_ERR_STATE, "no state yet");
     const size_t n = (size_t)h->nx * h->ny;
@@ -933,6 +938,7 @@ int wave2d_get_state(wave2d_t h, double* u_prev, double* u_cur, int64_t* k) {
 }
 
 int wave2d_set_state(wave2d_t h, const double* u_prev, const double* u_cur, int64_t k, int on_device) {
+    NvtxRange nvtx_range("wave2d_set_state");
     if (!h || !u_prev || !u_cur) return set_error(WAVE2D_ERR_ARG, "null argument");
     if (k < 1) return set_error(WAVE2D_ERR_ARG, "level index k must be >= 1");
     const size_t n = (size_t)h->nx * h->ny;
@@ -1016,6 +1022,7 @@ int wave2d_set_raw(wave2d_t h, const void* src, int64_t bytes, int64_t k) {
 }
 
 int wave2d_autotune(wave2d_t h, int64_t steps, wave2d_tune* best) {
+    NvtxRange nvtx_range("wave2d_autotune");
     if (!h) return set_error(WAVE2D_ERR_ARG, "null handle");
     if (steps < 1) return set_error(WAVE2D_ERR_ARG, "autotune needs steps >= 1");
     if (!h->initialized) return set_error(WAVE2D_ERR_STATE, "autotune needs an initialised state");

@@ -8,6 +8,8 @@
 #include <string>
 #include <type_traits>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/wave2d.h"
 #include "kernels.cuh"
 
@@ -30,6 +32,13 @@ void dev_free(const Allocator& a, void* p, size_t bytes, cudaStream_t s);
 extern std::atomic<int64_t> g_launches;
 
 constexpr int kGhost = 16;  // ghost ring width (elements) on every side
+
+// NVTX range around a library call (visible to profilers that record NVTX,
+// e.g. ncu --nvtx --nvtx-include "wave2d_step_n/"); costs nothing without one.
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
 
 inline size_t round_up(size_t v, size_t m) { return (v + m - 1) / m * m; }
 
