@@ -78,6 +78,8 @@ def _load():
         lib.oracle_error_sums.argtypes = [dp, i, i, d, d, i, dp, d, d, dp]
         lib.oracle_error_sums.restype = None
         lib.oracle_set_threads.argtypes = [i]
+        ip = ctypes.POINTER(ctypes.c_int)
+        lib.oracle_run_nodes.argtypes = [i, i, i, i, ip, ip, dp, dp, d, dp, dp, i64, dp, dp]
         for name in ("oracle_coeffs", "oracle_first_step", "oracle_two_step", "oracle_run",
                      "oracle_continue", "oracle_set_threads"):
             getattr(lib, name).restype = ctypes.c_int
@@ -167,6 +169,32 @@ def continue_run(scheme, u_prev, u_cur, lam, n_more, bc=BC_ZERO, conventional=Fa
                                _ptr(a), _ptr(b), int(n_more)) != 0:
         raise ValueError("bad arguments")
     return a, b
+
+
+def run_nodes(nodes, wa, wb, u0, v0, tau, n_t, bc=BC_ZERO):
+    """The algorithm of Section 3 in node-weight form (any derived stencil):
+    u^1 = sum_q wa_q u^0_{.+q} + tau sum_q wb_q v^0_{.+q}, then
+    u^{k+1} = 2 sum_q wa_q u^k_{.+q} - u^{k-1}.  ``nodes`` are (q1, q2)
+    offsets, ``wa`` / ``wb`` the weights A phi_q and B phi_q / tau evaluated
+    at the Courant number.  Returns (u^{n_t-1}, u^{n_t})."""
+    u0 = np.ascontiguousarray(u0, dtype=np.float64)
+    ny, nx = u0.shape
+    v0 = _field(v0, ny, nx)
+    q1 = np.ascontiguousarray([q[0] for q in nodes], dtype=np.intc)
+    q2 = np.ascontiguousarray([q[1] for q in nodes], dtype=np.intc)
+    wa = np.ascontiguousarray(wa, dtype=np.float64)
+    wb = np.ascontiguousarray(wb, dtype=np.float64)
+    if not (len(q1) == len(wa) == len(wb)):
+        raise ValueError("nodes and weights differ in length")
+    up = np.empty_like(u0)
+    uc = np.empty_like(u0)
+    ip = ctypes.POINTER(ctypes.c_int)
+    rc = _load().oracle_run_nodes(bc, nx, ny, len(q1), q1.ctypes.data_as(ip), q2.ctypes.data_as(ip),
+                                  _ptr(wa), _ptr(wb), float(tau), _ptr(u0), _ptr(v0), int(n_t),
+                                  _ptr(up), _ptr(uc))
+    if rc != 0:
+        raise ValueError("bad arguments")
+    return up, uc
 
 
 def error_sums(u, h, x_off, exact, exact_params, c, t):

@@ -169,3 +169,60 @@ def delta_coefficients(scheme: int):
         a.append({k: 2 * v for k, v in pa.items()})
         b.append(wb.get(s, {}))
     return a, b
+
+
+# ---------------------------------------------------------------------------
+# Derived schemes beyond Section 6.  Larger segments M*_{<=m} give further
+# stencils; where the weights are symmetric under the eight symmetries of the
+# square they group into classes, a class being every node (+-q1, +-q2),
+# (+-q2, +-q1) with q1 > 0, 0 <= q2 <= q1 (4 nodes if q2 == 0 or q2 == q1,
+# else 8).  A class is named by (q1, q2).
+# ---------------------------------------------------------------------------
+def class_of(node: Tuple[int, int]) -> Tuple[int, int]:
+    a, b = abs(node[0]), abs(node[1])
+    return (max(a, b), min(a, b))
+
+
+def class_nodes(cls: Tuple[int, int]) -> List[Tuple[int, int]]:
+    q1, q2 = cls
+    out = set()
+    for a, b in ((q1, q2), (q2, q1)):
+        for s1 in (1, -1):
+            for s2 in (1, -1):
+                out.add((s1 * a, s2 * b))
+    return sorted(out)
+
+
+def node_weights(m: int, lam: float):
+    """(nodes, wa, wb) at Courant number lam for the segment M*_{<=m}, nodes
+    with a non-zero weight polynomial only: wa = A phi_q, wb = B phi_q / tau."""
+    nodes, wa, wb, _ = stencil_weights(m)
+    keep = [q for q in nodes if wa[q] or wb[q]]
+    return keep, [evaluate(wa[q], lam) for q in keep], [evaluate(wb[q], lam) for q in keep]
+
+
+def class_scheme(m: int):
+    """The stencil of the segment M*_{<=m} in class form.
+
+    Returns (classes, a, b): the two-step adds sum_c a_c delta_c(u^k) and the
+    first step a_c / 2 delta_c(u^0) + tau b_c delta_c(v^0), where delta_c is
+    the sum of a level over the class's nodes minus (number of nodes) times
+    the centre value; a_c = 2 A phi_q, b_c = B phi_q / tau (any q in c), as
+    polynomials in lambda.  Classes are sorted by (radius, q2).  Raises
+    ValueError if the weights are not symmetric."""
+    nodes, wa, wb, _ = stencil_weights(m)
+    groups: Dict[Tuple[int, int], List[Tuple[int, int]]] = {}
+    for q in nodes:
+        if q != (0, 0) and (wa[q] or wb[q]):
+            groups.setdefault(class_of(q), []).append(q)
+    classes = sorted(groups, key=lambda c: (c[0], c[1]))
+    a, b = [], []
+    for cls in classes:
+        members = class_nodes(cls)
+        pa, pb = wa.get(members[0], {}), wb.get(members[0], {})
+        for q in members:
+            if wa.get(q, {}) != pa or wb.get(q, {}) != pb:
+                raise ValueError(f"segment {m}: weights are not symmetric on class {cls}")
+        a.append({k: 2 * v for k, v in pa.items()})
+        b.append(dict(pb))
+    return classes, a, b

@@ -60,6 +60,18 @@ def symbol(coef, th1: float, th2: float) -> float:
     return coef[0] * d10 + coef[1] * d11 + coef[2] * d20
 
 
+def class_symbol(classes, coef, th1: float, th2: float) -> float:
+    """Symbol of sum_c coef_c delta_c for a scheme in class form (a class
+    (q1, q2) being all nodes (+-q1, +-q2), (+-q2, +-q1)): each node q adds
+    cos(q . theta) - 1 = -2 sin^2(q . theta / 2)."""
+    total = 0.0
+    for cls, a in zip(classes, coef):
+        q1, q2 = cls
+        nodes = {(s1 * u, s2 * v) for u, v in ((q1, q2), (q2, q1)) for s1 in (1, -1) for s2 in (1, -1)}
+        total += a * sum(-2.0 * math.sin((n1 * th1 + n2 * th2) / 2) ** 2 for n1, n2 in nodes)
+    return total
+
+
 def _chebyshev_ratio(n: int, phi: float, cphi: float) -> float:
     """sin(n phi) / sin(phi), continuous at sin(phi) = 0."""
     s = math.sin(phi)
@@ -79,7 +91,20 @@ def amplitudes(scheme, lam, tau, k1, k2, h, n, a0=1.0, b0=0.0, c0=0.0, d0=None, 
         d0 = c * math.hypot(k1, k2)
     a, b = section6_coeffs(scheme, lam, conventional)
     th1, th2 = k1 * h, k2 * h
-    sa, sb = symbol(a, th1, th2), symbol(b, th1, th2)
+    return _amplitudes(symbol(a, th1, th2), symbol(b, th1, th2), tau, n, a0, b0, c0, d0)
+
+
+def class_amplitudes(classes, a, b, tau, k1, k2, h, n, a0=1.0, b0=0.0, c0=0.0, d0=None, c=1.0):
+    """(A_n, B_n) for a scheme in class form with coefficient values a, b
+    (evaluated at the Courant number); defaults as in ``amplitudes``."""
+    if d0 is None:
+        d0 = c * math.hypot(k1, k2)
+    th1, th2 = k1 * h, k2 * h
+    return _amplitudes(class_symbol(classes, a, th1, th2), class_symbol(classes, b, th1, th2), tau, n,
+                       a0, b0, c0, d0)
+
+
+def _amplitudes(sa, sb, tau, n, a0, b0, c0, d0):
     A1 = (1 + sa / 2) * a0 + tau * (1 + sb) * c0
     B1 = (1 + sa / 2) * b0 + tau * (1 + sb) * d0
     if n == 0:
@@ -95,6 +120,32 @@ def amplitudes(scheme, lam, tau, k1, k2, h, n, a0=1.0, b0=0.0, c0=0.0, d0=None, 
     r = _chebyshev_ratio(n, phi, cphi)
     cn = math.cos(n * phi)
     return a0 * cn + (A1 - a0 * cphi) * r, b0 * cn + (B1 - b0 * cphi) * r
+
+
+def stability_limit(classes, a_of_lam, n_theta: int = 257, lam_hi: float = 2.0) -> float:
+    """Largest Courant number lam such that every lam' <= lam keeps the
+    symbol of the two-step in [-4, 0] on an n_theta x n_theta grid of
+    [0, pi]^2 (von Neumann: the roots of g^2 - (2 + S) g + 1 stay on the
+    unit circle).  a_of_lam(lam) returns the class coefficients."""
+    th = np.linspace(0.0, math.pi, n_theta)
+    T1, T2 = np.meshgrid(th, th, indexing="ij")
+    sig = []
+    for q1, q2 in classes:
+        nodes = {(s1 * u, s2 * v) for u, v in ((q1, q2), (q2, q1)) for s1 in (1, -1) for s2 in (1, -1)}
+        sig.append(sum(-2.0 * np.sin((n1 * T1 + n2 * T2) / 2) ** 2 for n1, n2 in nodes))
+
+    def stable(lam):
+        S = sum(ac * sg for ac, sg in zip(a_of_lam(lam), sig))
+        return bool(np.all(S >= -4.0 - 1e-13) and np.all(S <= 1e-13))
+
+    step, lam = 1.0 / 512, 0.0
+    while lam + step <= lam_hi and stable(lam + step):
+        lam += step
+    lo, hi = lam, lam + step
+    for _ in range(60):
+        mid = 0.5 * (lo + hi)
+        lo, hi = (mid, hi) if stable(mid) else (lo, mid)
+    return lo
 
 
 def field(scheme, lam, tau, k1, k2, h, nx, ny, n, x_off=0.0, **kw) -> np.ndarray:
