@@ -141,6 +141,10 @@ typedef struct {
     int64_t device_bytes;
     int32_t kernel;  /* two-step kernel currently selected (WAVE2D_KERNEL_*)  */
     int32_t temporal_t;
+    int32_t n_classes;  /* derived schemes: classes in use (0 for scheme 5/9/13) */
+    int32_t n_points;   /* stencil nodes, centre included                        */
+    double class_a[8];  /* derived schemes: a_c as used, in chain order          */
+    double class_b[8];  /* derived schemes: b_c as used                          */
 } wave2d_info_t;
 
 /* ------------------------------------------------------------------------ */
@@ -161,6 +165,62 @@ int wave2d_set_allocator(wave2d_alloc_fn alloc, wave2d_free_fn release, void *ct
  * lambda_max * (1 + 1e-12) without WAVE2D_ALLOW_UNSTABLE), WAVE2D_ERR_OOM. */
 int wave2d_create(const wave2d_grid *grid, double h, double tau, double c, int scheme,
                   wave2d_t *out);
+
+/* ------------------------------------------------------------------------ */
+/* Derived schemes.  Sections 4-5 build a stencil from any initial segment    */
+/* M*_{<=m} of the monomials ordered by Eq. g: the nodes are the McKinney      */
+/* images (Eq. alpha / invMcKinney) of the monomials, the weights A phi_q and  */
+/* B phi_q of the Lagrange basis of Eq. Lagrange follow from the inverse of    */
+/* the matrix D of Eq. matrix1 and the exact integrals of Eq. exact1 / exact2.*/
+/* m = 6, 11, 15 give the 5-, 9- and 13-point schemes of Section 6; larger     */
+/* segments give further schemes.  When the weights are symmetric under the   */
+/* eight symmetries of the square they group into classes: class (q1, q2),    */
+/* q1 > 0, 0 <= q2 <= q1, is the set of nodes (+-q1, +-q2), (+-q2, +-q1)       */
+/* (4 nodes if q2 == 0 or q2 == q1, else 8), and                              */
+/*   Lambda_a(w) = sum_c a_c delta_c(w),  delta_c(w) = sum_{q in c} w_{.+q} - n_c w. */
+/* Segments up to m = 49 use the classes of the chain, in this order:         */
+/*   c = 0..7:  (1,0) (1,1) (2,0) (2,1) (3,0) (2,2) (3,1) (4,0)                */
+/* (m = 24: 21 points, 28: 25, 37: 29, 41: 37, 45: 41); a scheme uses the     */
+/* first n_classes of them, a class it lacks having zero coefficients.        */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    int32_t segment;    /* m of the segment it was derived from; 0 if supplied   */
+    int32_t n_classes;  /* 1..8: the first n_classes classes of the chain        */
+    int32_t radius;     /* stencil radius (largest q1 in use)                    */
+    int32_t n_points;   /* stencil nodes with a non-zero weight, centre included */
+    double a[8][9];     /* a_c(lambda) = sum_p a[c][p] lambda^p  (two-step)      */
+    double b[8][9];     /* b_c(lambda) = sum_p b[c][p] lambda^p  (first step, v) */
+} wave2d_scheme;
+
+/* Derive the scheme of the segment M*_{<=m} (host only, no GPU needed): the
+ * derivation above in FP64 (Gaussian elimination with partial pivoting and
+ * two rounds of refinement whose residuals are computed with compensated
+ * products and sums; the entries of D are small integers, held exactly),
+ * a_c = 2 A phi_q and
+ * b_c = B phi_q / tau as polynomials in lambda, coefficients below 1e-13 of
+ * the largest dropped to zero.  Errors: WAVE2D_ERR_ARG for m outside 1..49,
+ * a segment whose nodes are not distinct or whose D is singular, weights
+ * that are not symmetric (e.g. m = 14, 23, 27, 40, 44) or a segment with no
+ * class at all (m <= 4). */
+int wave2d_derive_scheme(int32_t m, wave2d_scheme *out);
+
+/* Stability limit of a scheme (host only): the largest lambda such that for
+ * every lambda' <= lambda the symbol S(theta) = sum_c a_c(lambda') sigma_c(theta),
+ * sigma_c(theta) = sum_{q in c} (cos(q . theta) - 1), stays in [-4, 0] on a
+ * 129 x 129 grid of theta in [0, pi]^2 (von Neumann: the roots of
+ * g^2 - (2 + S) g + 1 then lie on the unit circle), found by a scan in steps
+ * of 1/512 up to lambda = 2 and 60 bisections.  For m = 6, 11, 15 it returns
+ * the Section 6 limits to 1e-12.  *out = 0 if even lambda = 1/512 is unstable. */
+int wave2d_scheme_lambda_max(const wave2d_scheme *s, double *out);
+
+/* Create a simulation of a derived (or caller-supplied) scheme; otherwise as
+ * wave2d_create.  The coefficients are evaluated at lambda = c tau / h in
+ * FP64.  The two-step runs on the one-node kernel or the TMA kernel
+ * (WAVE2D_KERNEL_TEMPORAL is not available: WAVE2D_ERR_ARG from
+ * wave2d_set_tuning); grid.flags may not hold WAVE2D_CONVENTIONAL.  Errors as
+ * wave2d_create, with the stability limit of wave2d_scheme_lambda_max. */
+int wave2d_create_scheme(const wave2d_grid *grid, double h, double tau, double c,
+                         const wave2d_scheme *s, wave2d_t *out);
 
 /* First time step (Eq. A1 in the discrete forms comp5.1, comp9.1, comp13.1):
  * u0, v0 are nx*ny FP64 arrays, in host memory (on_device = 0) or device

@@ -17,10 +17,12 @@ CSRC = os.path.join(PKG, "csrc")
 OUT = os.path.join(PKG, "libwave2d.so")
 OBJ = os.path.join(PKG, "_objs")
 
+# Host code is compiled without floating-point contraction so that it rounds
+# the same way on x86-64 and aarch64 hosts.
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
-              "-Xcompiler", "-fPIC", "-I" + os.path.join(ROOT, "include")]
+              "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off", "-I" + os.path.join(ROOT, "include")]
 
-SOURCES = ["wave2d.cu", "noalloc.cu", "batch.cu", "server.cu"]
+SOURCES = ["wave2d.cu", "chain.cu", "scheme.cu", "noalloc.cu", "batch.cu", "server.cu"]
 
 
 def _nvcc():

@@ -15,6 +15,7 @@
 #include <vector>
 
 #include "kernels_temporal.cuh"
+#include "stencil_chain.cuh"
 #include "wave2d_impl.cuh"
 
 namespace w2d {
@@ -36,19 +37,6 @@ int cuda_fail(cudaError_t e, const char* what) {
     return set_error(e == cudaErrorMemoryAllocation ? WAVE2D_ERR_OOM : WAVE2D_ERR_CUDA, "%s: %s (%s)",
                      what, cudaGetErrorString(e), cudaGetErrorName(e));
 }
-
-#define W2D_CUDA(call, what)                      \
-    do {                                          \
-        cudaError_t e_ = (call);                  \
-        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
-    } while (0)
-
-#define W2D_LAUNCHED(what)                                   \
-    do {                                                     \
-        cudaError_t e_ = cudaGetLastError();                 \
-        if (e_ != cudaSuccess) return cuda_fail(e_, what);   \
-        g_launches.fetch_add(1, std::memory_order_relaxed);  \
-    } while (0)
 
 std::atomic<int64_t> g_launches{0};
 
@@ -219,11 +207,15 @@ static int prepare_tma(wave2d* h) {
     if (h->dtype == DT_F32X2) return set_error(WAVE2D_ERR_ARG, "TMA kernel supports F32 and F64 storage");
     int bw = 0, bh = 0, tw = 0;
     int rc = WAVE2D_OK;
-    dispatch_s(h->scheme, [&](auto Sc) {
-        constexpr int S = decltype(Sc)::value;
-        if (h->dtype == DT_F32) tma_box<float, S, 32>(bw, bh, tw);
-        else tma_box<double, S, 32>(bw, bh, tw);
-    });
+    if (h->nclass > 0) {
+        chain_tma_box(h, bw, bh, tw);
+    } else {
+        dispatch_s(h->scheme, [&](auto Sc) {
+            constexpr int S = decltype(Sc)::value;
+            if (h->dtype == DT_F32) tma_box<float, S, 32>(bw, bh, tw);
+            else tma_box<double, S, 32>(bw, bh, tw);
+        });
+    }
     for (int p = 0; p < h->nlevels && rc == WAVE2D_OK; ++p) {
         rc = encode_plane(&h->tm_cur[p], h->hi[p], h, bw, bh);
         if (rc == WAVE2D_OK) rc = encode_plane(&h->tm_prev[p], h->hi[p], h, tw, 32);
@@ -315,6 +307,7 @@ static int launch_first_step(wave2d* h, const double* du0, const double* dv0) {
     const Coef3<double> ca = coef_as<double>(ahalf), cb = coef_as<double>(h->b);
     const ExactTab ex = make_tab(h, h->tab_track, h->track_ex, h->tau);
     const Reduce rd = make_reduce(h, h->acc_track, 1);
+    if (h->nclass > 0) return chain_first_step(h, du0, dv0, ex, rd);
     const Level L0 = h->level(1), L1 = h->level(0);  // u^0 -> plane 1 (u^{k-1}), u^1 -> plane 0
     dispatch_dt(h->dtype, [&](auto DTc) {
         dispatch_s(h->scheme, [&](auto Sc) {
@@ -335,6 +328,7 @@ static int launch_simple_step(wave2d* h, bool track) {
     const Level cur = h->level(h->cur), nxt = h->level(h->prv);
     const ExactTab ex = track ? make_tab(h, h->tab_track, h->track_ex, (double)(h->k + 1) * h->tau) : ExactTab{};
     const Reduce rd = make_reduce(h, h->acc_track, 1);
+    if (h->nclass > 0) return chain_simple_step(h, track, ex, rd);
     dispatch_dt(h->dtype, [&](auto DTc) {
         constexpr int DT = decltype(DTc)::value;
         using V = typename St<DT>::V;
@@ -384,6 +378,7 @@ static int launch_tma_t(wave2d* h) {
 }
 
 static int launch_tma_step(wave2d* h) {
+    if (h->nclass > 0) return chain_tma_step(h);
     int rc = WAVE2D_OK;
     dispatch_s(h->scheme, [&](auto Sc) {
         constexpr int S = decltype(Sc)::value;
@@ -487,7 +482,7 @@ static int select_kernel(wave2d* h) {
         want = (h->dtype == DT_F32 && (int64_t)h->nx * h->ny >= 65536) ? WAVE2D_KERNEL_TMA
                                                                        : WAVE2D_KERNEL_SIMPLE;
     }
-    if (want == WAVE2D_KERNEL_TEMPORAL && h->dtype != DT_F32) want = WAVE2D_KERNEL_TMA;
+    if (want == WAVE2D_KERNEL_TEMPORAL && (h->dtype != DT_F32 || h->nclass > 0)) want = WAVE2D_KERNEL_TMA;
     if (want == WAVE2D_KERNEL_TMA && h->dtype == DT_F32X2) want = WAVE2D_KERNEL_SIMPLE;
     if ((want == WAVE2D_KERNEL_TMA || want == WAVE2D_KERNEL_TEMPORAL) && !h->tma_ready) {
         int rc = prepare_tma(h);
@@ -644,60 +639,32 @@ static void release_handle(wave2d* h) {
     delete h;
 }
 
-int wave2d_create(const wave2d_grid* grid, double hh, double tau, double c, int scheme, wave2d_t* out) {
-    NvtxRange nvtx_range("wave2d_create");
-    if (!grid || !out) return set_error(WAVE2D_ERR_ARG, "null argument");
-    *out = nullptr;
-    if (scheme != 5 && scheme != 9 && scheme != 13)
-        return set_error(WAVE2D_ERR_ARG, "scheme must be 5, 9 or 13 (got %d)", scheme);
+// Validation shared by both constructors.
+static int check_grid(const wave2d_grid* grid, double hh, double tau, double c, int allowed_flags) {
     if (grid->nx < 1 || grid->ny < 1 || grid->nx > 65536 || grid->ny > 65536)
         return set_error(WAVE2D_ERR_ARG, "grid size %d x %d outside 1..65536", grid->nx, grid->ny);
     if (grid->bc != WAVE2D_BC_ZERO && grid->bc != WAVE2D_BC_PERIODIC)
         return set_error(WAVE2D_ERR_ARG, "unknown boundary condition %d", grid->bc);
     if (grid->dtype != WAVE2D_F64 && grid->dtype != WAVE2D_F32 && grid->dtype != WAVE2D_F32X2)
         return set_error(WAVE2D_ERR_ARG, "unknown dtype %d", grid->dtype);
-    if (grid->flags & ~(WAVE2D_ALLOW_UNSTABLE | WAVE2D_CONVENTIONAL))
-        return set_error(WAVE2D_ERR_ARG, "unknown flags 0x%x", grid->flags);
+    if (grid->flags & ~allowed_flags) return set_error(WAVE2D_ERR_ARG, "unsupported flags 0x%x", grid->flags);
     if (!(hh > 0) || !(tau > 0) || !(c > 0) || !std::isfinite(hh) || !std::isfinite(tau) || !std::isfinite(c))
         return set_error(WAVE2D_ERR_ARG, "h, tau and c must be positive and finite");
-    const bool conventional = (grid->flags & WAVE2D_CONVENTIONAL) != 0;
-    const double lam = c * tau / hh;
-    const double lmax = lambda_max_of(scheme, conventional);
-    if (lam > lmax * (1.0 + 1e-12) && !(grid->flags & WAVE2D_ALLOW_UNSTABLE))
-        return set_error(WAVE2D_ERR_UNSTABLE, "Courant number %.17g exceeds the stability limit %.17g of the %d-point scheme",
-                         lam, lmax, scheme);
+    return WAVE2D_OK;
+}
 
-    wave2d* h = new (std::nothrow) wave2d();
-    if (!h) return set_error(WAVE2D_ERR_OOM, "host allocation failed");
-    h->nx = grid->nx;
-    h->ny = grid->ny;
-    h->bc = grid->bc;
-    h->dtype = grid->dtype;
-    h->flags = grid->flags;
-    h->scheme = scheme;
-    h->R = scheme == 13 ? 2 : 1;
-    h->h = hh;
-    h->tau = tau;
-    h->c = c;
-    h->lam = lam;
-    h->lam_max = lmax;
-    scheme_coefficients(scheme, conventional, lam, h->a, h->b);
+// Device side of a new handle whose problem fields (sizes, scheme,
+// coefficients, radius) are set: stream, level planes, scratch, kernel.
+static int create_device_state(wave2d* h, const wave2d_grid* grid) {
     h->alloc = current_allocator();
-
     cudaError_t e = cudaGetDevice(&h->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->l2_bytes, cudaDevAttrL2CacheSize, h->device);
-    if (e != cudaSuccess) {
-        delete h;
-        return cuda_fail(e, "no usable CUDA device");
-    }
+    if (e != cudaSuccess) return cuda_fail(e, "no usable CUDA device");
     h->stream = (cudaStream_t)grid->stream;
     if (!h->stream) {
         e = cudaStreamCreate(&h->stream);
-        if (e != cudaSuccess) {
-            delete h;
-            return cuda_fail(e, "stream create");
-        }
+        if (e != cudaSuccess) return cuda_fail(e, "stream create");
         h->own_stream = true;
     }
 
@@ -705,7 +672,7 @@ int wave2d_create(const wave2d_grid* grid, double hh, double tau, double c, int 
     // (the temporal kernel writes out of place); FP32x2 keeps hi and lo
     // planes of two levels; FP64 two levels.
     h->elem = (h->dtype == WAVE2D_F64) ? 8 : 4;
-    h->nlevels = (h->dtype == WAVE2D_F32) ? 4 : 2;
+    h->nlevels = (h->dtype == WAVE2D_F32 && h->nclass == 0) ? 4 : 2;
     h->gw = h->R;
     h->G = kGhost;
     h->pitch = (int)round_up((size_t)h->nx + 2 * kGhost, 32);
@@ -720,10 +687,7 @@ int wave2d_create(const wave2d_grid* grid, double hh, double tau, double c, int 
                            2 * round_up(tab_doubles * sizeof(double), 256);
     h->base_bytes = nplanes * h->plane_bytes + scratch;
     h->base = dev_alloc(h->alloc, h->base_bytes, h->stream);
-    if (!h->base) {
-        release_handle(h);
-        return set_error(WAVE2D_ERR_OOM, "device allocation of %zu bytes failed", h->base_bytes);
-    }
+    if (!h->base) return set_error(WAVE2D_ERR_OOM, "device allocation of %zu bytes failed", h->base_bytes);
     char* p = (char*)h->base;
     for (int q = 0; q < h->nlevels; ++q) h->hi[q] = p + q * h->plane_bytes;
     if (h->dtype == WAVE2D_F32X2)
@@ -743,12 +707,86 @@ int wave2d_create(const wave2d_grid* grid, double hh, double tau, double c, int 
     p += round_up(tab_doubles * sizeof(double), 256);
     h->tab_track = (double*)p;
     e = cudaMemsetAsync(h->base, 0, h->base_bytes, h->stream);
-    if (e != cudaSuccess) {
-        int rc = cuda_fail(e, "memset");
+    if (e != cudaSuccess) return cuda_fail(e, "memset");
+    return select_kernel(h);
+}
+
+static void set_problem(wave2d* h, const wave2d_grid* grid, double hh, double tau, double c) {
+    h->nx = grid->nx;
+    h->ny = grid->ny;
+    h->bc = grid->bc;
+    h->dtype = grid->dtype;
+    h->flags = grid->flags;
+    h->h = hh;
+    h->tau = tau;
+    h->c = c;
+    h->lam = c * tau / hh;
+}
+
+int wave2d_create(const wave2d_grid* grid, double hh, double tau, double c, int scheme, wave2d_t* out) {
+    NvtxRange nvtx_range("wave2d_create");
+    if (!grid || !out) return set_error(WAVE2D_ERR_ARG, "null argument");
+    *out = nullptr;
+    if (scheme != 5 && scheme != 9 && scheme != 13)
+        return set_error(WAVE2D_ERR_ARG, "scheme must be 5, 9 or 13 (got %d)", scheme);
+    int rc = check_grid(grid, hh, tau, c, WAVE2D_ALLOW_UNSTABLE | WAVE2D_CONVENTIONAL);
+    if (rc != WAVE2D_OK) return rc;
+    const bool conventional = (grid->flags & WAVE2D_CONVENTIONAL) != 0;
+    const double lam = c * tau / hh;
+    const double lmax = lambda_max_of(scheme, conventional);
+    if (lam > lmax * (1.0 + 1e-12) && !(grid->flags & WAVE2D_ALLOW_UNSTABLE))
+        return set_error(WAVE2D_ERR_UNSTABLE, "Courant number %.17g exceeds the stability limit %.17g of the %d-point scheme",
+                         lam, lmax, scheme);
+
+    wave2d* h = new (std::nothrow) wave2d();
+    if (!h) return set_error(WAVE2D_ERR_OOM, "host allocation failed");
+    set_problem(h, grid, hh, tau, c);
+    h->scheme = scheme;
+    h->R = scheme == 13 ? 2 : 1;
+    h->npoints = scheme;
+    h->lam_max = lmax;
+    scheme_coefficients(scheme, conventional, lam, h->a, h->b);
+    rc = create_device_state(h, grid);
+    if (rc != WAVE2D_OK) {
         release_handle(h);
         return rc;
     }
-    int rc = select_kernel(h);
+    *out = h;
+    return WAVE2D_OK;
+}
+
+int wave2d_create_scheme(const wave2d_grid* grid, double hh, double tau, double c, const wave2d_scheme* s,
+                         wave2d_t* out) {
+    NvtxRange nvtx_range("wave2d_create_scheme");
+    if (!grid || !out) return set_error(WAVE2D_ERR_ARG, "null argument");
+    *out = nullptr;
+    int rc = check_scheme(s);
+    if (rc != WAVE2D_OK) return rc;
+    rc = check_grid(grid, hh, tau, c, WAVE2D_ALLOW_UNSTABLE);
+    if (rc != WAVE2D_OK) return rc;
+    const double lam = c * tau / hh;
+    const double lmax = scheme_lambda_max(s);
+    if (lam > lmax * (1.0 + 1e-12) && !(grid->flags & WAVE2D_ALLOW_UNSTABLE))
+        return set_error(WAVE2D_ERR_UNSTABLE, "Courant number %.17g exceeds the stability limit %.17g of the derived scheme",
+                         lam, lmax);
+    wave2d* h = new (std::nothrow) wave2d();
+    if (!h) return set_error(WAVE2D_ERR_OOM, "host allocation failed");
+    set_problem(h, grid, hh, tau, c);
+    h->scheme = 0;
+    h->nclass = s->n_classes;
+    h->R = chain_radius(s->n_classes);
+    h->npoints = chain_points(s->n_classes);
+    if (s->n_points > 0) h->npoints = s->n_points;
+    h->lam_max = lmax;
+    for (int q = 0; q < s->n_classes; ++q) {
+        h->ca[q] = poly_at(s->a[q], lam);
+        h->cb[q] = poly_at(s->b[q], lam);
+    }
+    for (int q = 0; q < 3 && q < s->n_classes; ++q) {
+        h->a[q] = h->ca[q];
+        h->b[q] = h->cb[q];
+    }
+    rc = create_device_state(h, grid);
     if (rc != WAVE2D_OK) {
         release_handle(h);
         return rc;
@@ -765,6 +803,8 @@ int wave2d_set_tuning(wave2d_t h, const wave2d_tune* tune) {
         return set_error(WAVE2D_ERR_ARG, "unknown kernel %d", tune->kernel);
     if (tune->kernel == WAVE2D_KERNEL_TMA && h->dtype == WAVE2D_F32X2)
         return set_error(WAVE2D_ERR_ARG, "the TMA kernel supports F32 and F64 storage only");
+    if (tune->kernel == WAVE2D_KERNEL_TEMPORAL && h->nclass > 0)
+        return set_error(WAVE2D_ERR_ARG, "the temporal kernel covers the 5-, 9- and 13-point schemes only");
     if (tune->ctas_per_sm < 0 || tune->ctas_per_sm > 32)
         return set_error(WAVE2D_ERR_ARG, "ctas_per_sm must be 0 (auto) or 1..32");
     h->tune = *tune;
@@ -795,6 +835,12 @@ int wave2d_get_info(wave2d_t h, wave2d_info_t* info) {
     info->device_bytes = (int64_t)h->base_bytes;
     info->kernel = h->kernel;
     info->temporal_t = (h->kernel == WAVE2D_KERNEL_TEMPORAL) ? h->temporal_t : 1;
+    info->n_classes = h->nclass;
+    info->n_points = h->npoints;
+    for (int q = 0; q < 8; ++q) {
+        info->class_a[q] = h->ca[q];
+        info->class_b[q] = h->cb[q];
+    }
     return WAVE2D_OK;
 }
 
@@ -1036,7 +1082,11 @@ int wave2d_autotune(wave2d_t h, int64_t steps, wave2d_tune* best) {
         t.ctas_per_sm = per_sm;
         cands.push_back(t);
     };
-    if (h->dtype == WAVE2D_F32) {
+    if (h->dtype == WAVE2D_F32 && h->nclass > 0) {
+        add(WAVE2D_KERNEL_TMA, 0, 0, 1);
+        add(WAVE2D_KERNEL_TMA, 0, 0, 2);
+        add(WAVE2D_KERNEL_SIMPLE, 0, 0, 0);
+    } else if (h->dtype == WAVE2D_F32) {
         add(WAVE2D_KERNEL_TMA, 0, 0, 1);
         add(WAVE2D_KERNEL_TMA, 0, 0, 2);
         for (int T : {2, 4})

@@ -42,6 +42,19 @@ struct NvtxRange {
 
 inline size_t round_up(size_t v, size_t m) { return (v + m - 1) / m * m; }
 
+#define W2D_CUDA(call, what)                                   \
+    do {                                                       \
+        cudaError_t e_ = (call);                               \
+        if (e_ != cudaSuccess) return w2d::cuda_fail(e_, what); \
+    } while (0)
+
+#define W2D_LAUNCHED(what)                                         \
+    do {                                                           \
+        cudaError_t e_ = cudaGetLastError();                       \
+        if (e_ != cudaSuccess) return w2d::cuda_fail(e_, what);     \
+        w2d::g_launches.fetch_add(1, std::memory_order_relaxed);   \
+    } while (0)
+
 }  // namespace w2d
 
 struct wave2d {
@@ -49,6 +62,10 @@ struct wave2d {
     int nx = 0, ny = 0, bc = 0, dtype = 0, flags = 0, scheme = 0, R = 1;
     double h = 0, tau = 0, c = 0, lam = 0, lam_max = 0;
     double a[3] = {0, 0, 0}, b[3] = {0, 0, 0};
+    // derived schemes: number of classes of the chain in use (0 for the
+    // Section 6 schemes), stencil nodes, and the class coefficients at lambda
+    int nclass = 0, npoints = 0;
+    double ca[8] = {}, cb[8] = {};
     // device
     int device = 0, num_sms = 0, l2_bytes = 0;
     cudaStream_t stream = nullptr;
@@ -95,3 +112,17 @@ struct wave2d {
     w2d::Level level(int p) const { return w2d::Level{hi[p], lo[p]}; }
     w2d::Geo geo() const { return w2d::Geo{nx, ny, pitch, G}; }
 };
+
+namespace w2d {
+// Derived schemes (chain.cu): launches of the class-chain kernels for a
+// handle with nclass > 0.
+int chain_first_step(wave2d* h, const double* du0, const double* dv0, const ExactTab& ex, const Reduce& rd);
+int chain_simple_step(wave2d* h, bool track, const ExactTab& ex, const Reduce& rd);
+int chain_tma_step(wave2d* h);
+void chain_tma_box(const wave2d* h, int& box_w, int& box_h, int& tile_w);
+// Derivation and stability limit (scheme.cu).
+int derive_scheme(int m, wave2d_scheme* out);
+int check_scheme(const wave2d_scheme* s);
+double poly_at(const double* c, double lam);
+double scheme_lambda_max(const wave2d_scheme* s);
+}  // namespace w2d

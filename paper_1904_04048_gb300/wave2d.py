@@ -59,7 +59,24 @@ class wave2d_info_t(ctypes.Structure):
                 ("radius", ctypes.c_int32), ("dtype", ctypes.c_int32), ("bc", ctypes.c_int32),
                 ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("pitch", ctypes.c_int32),
                 ("ghost", ctypes.c_int32), ("device_bytes", ctypes.c_int64), ("kernel", ctypes.c_int32),
-                ("temporal_t", ctypes.c_int32)]
+                ("temporal_t", ctypes.c_int32), ("n_classes", ctypes.c_int32), ("n_points", ctypes.c_int32),
+                ("class_a", ctypes.c_double * 8), ("class_b", ctypes.c_double * 8)]
+
+
+# Classes of the derived schemes, in chain order (include/wave2d.h).
+CLASS_CHAIN = ((1, 0), (1, 1), (2, 0), (2, 1), (3, 0), (2, 2), (3, 1), (4, 0))
+
+
+class wave2d_scheme(ctypes.Structure):
+    _fields_ = [("segment", ctypes.c_int32), ("n_classes", ctypes.c_int32), ("radius", ctypes.c_int32),
+                ("n_points", ctypes.c_int32), ("a", (ctypes.c_double * 9) * 8), ("b", (ctypes.c_double * 9) * 8)]
+
+    def a_poly(self, c):
+        """Coefficients of a_c(lambda) by power 0..8."""
+        return [self.a[c][p] for p in range(9)]
+
+    def b_poly(self, c):
+        return [self.b[c][p] for p in range(9)]
 
 
 class wave2d_request(ctypes.Structure):
@@ -94,6 +111,10 @@ SIGNATURES = {
     "wave2d_set_allocator": (ctypes.c_int, [ALLOC_FN, FREE_FN, _P]),
     "wave2d_create": (ctypes.c_int, [ctypes.POINTER(wave2d_grid), ctypes.c_double, ctypes.c_double,
                                      ctypes.c_double, ctypes.c_int, ctypes.POINTER(_P)]),
+    "wave2d_derive_scheme": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(wave2d_scheme)]),
+    "wave2d_scheme_lambda_max": (ctypes.c_int, [ctypes.POINTER(wave2d_scheme), _D]),
+    "wave2d_create_scheme": (ctypes.c_int, [ctypes.POINTER(wave2d_grid), ctypes.c_double, ctypes.c_double,
+                                            ctypes.c_double, ctypes.POINTER(wave2d_scheme), ctypes.POINTER(_P)]),
     "wave2d_first_step": (ctypes.c_int, [_P, _P, _P, ctypes.c_int]),
     "wave2d_step_n": (ctypes.c_int, [_P, ctypes.c_int64]),
     "wave2d_error_vs_exact": (ctypes.c_int, [_P, ctypes.POINTER(wave2d_exact), _D, _D, _D]),
@@ -171,6 +192,19 @@ def lambda_max(scheme: int, conventional: bool = False) -> float:
     return lib().wave2d_lambda_max(scheme, int(conventional))
 
 
+def derive_scheme(m: int) -> wave2d_scheme:
+    """Scheme of the monomial segment M*_{<=m} (host-side derivation)."""
+    s = wave2d_scheme()
+    check(lib().wave2d_derive_scheme(int(m), ctypes.byref(s)))
+    return s
+
+
+def scheme_lambda_max(s: wave2d_scheme) -> float:
+    out = ctypes.c_double()
+    check(lib().wave2d_scheme_lambda_max(ctypes.byref(s), ctypes.byref(out)))
+    return out.value
+
+
 def error_norms_noalloc(field_ptr: int, dtype: int, nx: int, ny: int, ld: int, h: float, c: float,
                         t: float, ex: wave2d_exact | None = None, stream: int = 0):
     """(rel_l2, rel_linf) of a caller-owned device field through the
@@ -242,11 +276,16 @@ class Wave2D:
     """One simulation handle (``wave2d_t``)."""
 
     def __init__(self, nx, ny, h, tau, c=1.0, scheme=13, bc=BC_ZERO, dtype=F32, flags=0, stream=None):
+        """``scheme``: 5, 9 or 13 (Section 6), or a ``wave2d_scheme`` (derived)."""
         g = wave2d_grid(int(nx), int(ny), int(bc), int(dtype), int(flags), 0,
                         ctypes.c_void_p(int(stream) if stream else 0))
         out = ctypes.c_void_p()
-        check(lib().wave2d_create(ctypes.byref(g), float(h), float(tau), float(c), int(scheme),
-                                  ctypes.byref(out)))
+        if isinstance(scheme, wave2d_scheme):
+            check(lib().wave2d_create_scheme(ctypes.byref(g), float(h), float(tau), float(c),
+                                             ctypes.byref(scheme), ctypes.byref(out)))
+        else:
+            check(lib().wave2d_create(ctypes.byref(g), float(h), float(tau), float(c), int(scheme),
+                                      ctypes.byref(out)))
         self._h = out
         self.nx, self.ny = int(nx), int(ny)
 
