@@ -112,14 +112,17 @@ def test_tma_equals_simple_bitwise(w, m, dtype):
     u0, v0, h = smooth_ic(n, 150, BC_PERIODIC, seed=m)
     s = w.derive_scheme(m)
     lam = _lam(m)
-    raws = []
+    # the levels themselves (the TMA kernel also writes correct periodic
+    # images of whole vectors a little beyond the R rings the readers use,
+    # so the raw planes may differ in ghost cells nobody reads)
+    states = []
     for kernel in (w.KERNEL_SIMPLE, w.KERNEL_TMA):
         with w.Wave2D(n, 150, h, lam * h, scheme=s, bc=BC_PERIODIC, dtype=dtype) as sim:
             sim.set_tuning(kernel=kernel, use_graph=0)
             sim.first_step(u0, v0)
             sim.step_n(60)
-            raws.append(sim.get_raw()[0])
-    assert np.array_equal(raws[0], raws[1])
+            states.append(sim.get_state())
+    assert np.array_equal(states[0][0], states[1][0]) and np.array_equal(states[0][1], states[1][1])
 
 
 @pytest.mark.parametrize("bc", [BC_ZERO, BC_PERIODIC])
