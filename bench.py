@@ -42,6 +42,12 @@ WORKLOAD = ("9-point + 13-point schemes, FP32 storage, 4096^2 periodic grid, lam
             "2000 time levels each (first step + 1999 two-steps), 16 Gaussian pulses + band-limited "
             "noise (seed 2019), FP64 norm of the final field to host")
 
+# FP32 operations (add, subtract, multiply or fused multiply-add, one each) of
+# one two-step node-update as the schemes are written (Section 6): the class
+# sums of Eq. notations2 with their -4 u_ij terms, the products by the
+# coefficients, and 2 u^k - u^{k-1} + Lambda.
+FP32_OPS = {5: 9, 9: 14, 13: 19}
+
 # DRAM bytes (read + write) of one launch of a kernel at the benchmark size,
 # from an ncu capture of the same kernel source (see the profiles directory),
 # keyed by (kernel, hash of the kernel sources) so that a figure is dropped
@@ -320,6 +326,31 @@ def run_ours(args, rank, world, local_rank):
         effective = alg_bytes / avg_launch / 1e9
     achieved = alg_bytes / avg_launch / 1e9
     traffic = NCU_TRAFFIC.get((kname.split()[0], src_hash))
+    clocks = clk.summary()
+    hbm_view = {"bound": "hbm", "kernel": kname, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "peak_source": peak_src,
+                "algorithmic_bytes_per_launch": alg_bytes, "levels_per_launch": T,
+                "avg_launch_us": round(avg_launch * 1e6, 3), "traffic": traffic,
+                "unblocked_equivalent_gbs": round(effective, 1)}
+    if kernel == w.KERNEL_TEMPORAL:
+        # Temporal blocking takes the kernel off HBM (DRAM about 26 % busy in
+        # ncu); its limit is the FP32 pipe.  Algorithmic work: the two-step as
+        # written, FP32_OPS per node-update, T levels per launch, the two
+        # schemes' launches equally many.  Peak: one FP32 add, multiply or
+        # fused multiply-add per lane per clock, 128 lanes per SM.
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        mhz = clocks.get("sm_max_mhz") or 2070.0
+        alu_peak = sms * 128 * mhz * 1e6 / 1e12
+        alg_ops = T * N * N * sum(FP32_OPS[s] for s in SCHEMES) / len(SCHEMES)
+        alu = alg_ops / avg_launch / 1e12
+        roofline = {"bound": "alu", "kernel": kname, "achieved": round(alu, 2), "peak": round(alu_peak, 2),
+                    "unit": "TFLOP/s", "frac": round(alu / alu_peak, 4),
+                    "flop": "one FP32 add, multiply or fused multiply-add (one FP32-pipe lane slot)",
+                    "peak_source": f"{sms} SMs x 128 FP32 lanes x {mhz:.0f} MHz (maximum SM clock)",
+                    "algorithmic_flop_per_launch": int(alg_ops), "levels_per_launch": T,
+                    "avg_launch_us": round(avg_launch * 1e6, 3), "traffic": traffic, "hbm": hbm_view}
+    else:
+        roofline = hbm_view
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": "G point-updates/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(elapsed / args.steps * 1e3, 3),
@@ -330,12 +361,7 @@ def run_ours(args, rank, world, local_rank):
                    "point_updates_per_step": pts_step, "l2_flush_between_steps": True,
                    "autotuned": {str(s): tuned[s] for s in SCHEMES},
                    "parallelism": f"replicas x{world}"},
-        "roofline": {"bound": "hbm", "kernel": kname,
-                     "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                     "frac": round(achieved / peak, 4), "peak_source": peak_src,
-                     "algorithmic_bytes_per_launch": alg_bytes, "levels_per_launch": T,
-                     "avg_launch_us": round(avg_launch * 1e6, 3), "traffic": traffic,
-                     "unblocked_equivalent_gbs": round(effective, 1)},
+        "roofline": roofline,
         "per_scheme_ms_per_level": {str(s): round(per_scheme_stepn[s] / (args.steps * (STEPS_PER_SCHEME - 1)) * 1e3, 5)
                                     for s in SCHEMES},
         "e2e": {"value": round(e2e_value, 3), "unit": "G point-updates/s",
@@ -347,13 +373,14 @@ def run_ours(args, rank, world, local_rank):
                              "algorithmic_bytes_per_launch": 12 * N * N,
                              "traffic": NCU_TRAFFIC.get(("k2_tma", src_hash))}
                             if all(one_step[s] for s in SCHEMES) else None),
-        "clocks": clk.summary(),
+        "clocks": clocks,
         "result_norms": {str(s): [results[s][0], results[s][1]] for s in SCHEMES},
     }
     if world == 1 and not args.no_extras:
         line["config1"] = measure_config1(w, torch)
         line["batched"] = measure_batched(w, torch)
         line["served"] = measure_served(w, torch)
+        line["derived_schemes"] = measure_derived(w, torch, u0, v0, peak)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = time_oracle(u0, v0, args.cpu_budget)
     return line
@@ -504,20 +531,56 @@ def measure_config1(w, torch):
             "timing": "host wall clock per run incl. norm to host, 50 runs"}
 
 
-def profile_case(kernel: str, scheme: int):
+def measure_derived(w, torch, u0, v0, peak):
+    """Derived schemes (monomial segments m = 24, 28, 45: 21, 25 and 41
+    points) on the benchmark grid and inputs, FP32, lambda = 0.9 of each
+    scheme's limit: autotuned two-step kernel, 200 levels timed with CUDA
+    events on the handle's stream after 20 warm-up levels; HBM roofline at
+    12 B per node-update."""
+    from initial_data import BC_PERIODIC
+    out = {}
+    h = 1.0 / N
+    for m in (24, 28, 45):
+        s = w.derive_scheme(m)
+        lam = 0.9 * w.scheme_lambda_max(s)
+        stream = torch.cuda.Stream()
+        with w.Wave2D(N, N, h, lam * h, scheme=s, bc=BC_PERIODIC, dtype=w.F32, stream=stream.cuda_stream) as sim:
+            sim.first_step(u0, v0)
+            best = sim.autotune(steps=16)
+            sim.step_n(20)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            levels = 200
+            e0.record(stream)
+            sim.step_n(levels)
+            e1.record(stream)
+            e1.synchronize()
+            sec = e0.elapsed_time(e1) / 1e3 / levels
+        out[str(s.n_points)] = {"segment": m, "lambda": round(lam, 6), "us_per_level": round(sec * 1e6, 2),
+                                "value": round(N * N / sec / 1e9, 1), "unit": "G point-updates/s",
+                                "kernel": {1: "simple", 2: "tma", 3: "temporal"}.get(best.kernel),
+                                "hbm_frac": round(12 * N * N / sec / 1e9 / peak, 3)}
+    return out
+
+
+def profile_case(kernel: str, scheme: int, segment: int = 28):
     """A short run of one kernel at the benchmark size, for profiler captures:
     the first step, then a few launches of the named kernel on the
     benchmark's inputs (no timing, no JSON line).  4096^2 FP32 holds about
     0.5 GB on the device.
       k2_tma:      4 one-step launches (the first step comes before them)
-      k3_temporal: 3 launches of T = 4 levels, 32-row tiles"""
+      k3_temporal: 3 launches of T = 4 levels, 32-row tiles
+      kc2_tma:     4 one-step launches of a derived scheme (``segment``)"""
     from initial_data import BC_PERIODIC, LAMBDA_MAX, pulses_and_noise
     from paper_1904_04048_gb300 import wave2d as w
     u0, v0 = pulses_and_noise(N, seed=SEED)
     h = 1.0 / N
-    lam = 0.9 * LAMBDA_MAX[scheme]
+    if kernel == "kc2_tma":
+        scheme = w.derive_scheme(segment)
+        lam = 0.9 * w.scheme_lambda_max(scheme)
+    else:
+        lam = 0.9 * LAMBDA_MAX[scheme]
     with w.Wave2D(N, N, h, lam * h, scheme=scheme, bc=BC_PERIODIC, dtype=w.F32) as sim:
-        if kernel == "k2_tma":
+        if kernel in ("k2_tma", "kc2_tma"):
             sim.set_tuning(kernel=w.KERNEL_TMA, use_graph=0)
             levels = 4
         else:
@@ -526,7 +589,7 @@ def profile_case(kernel: str, scheme: int):
         sim.first_step(u0, v0)
         sim.step_n(levels)
         sim.sync()
-        print(f"profile case {kernel}, {scheme}-point, {N}^2: {levels} levels after the first step")
+        print(f"profile case {kernel}, {sim.info().n_points} points, {N}^2: {levels} levels after the first step")
 
 
 def run_reference(args, rank):
@@ -577,12 +640,13 @@ def main():
     ap.add_argument("--fixed-tuning", action="store_true",
                     help="skip the autotuner (temporal kernel, T = 4, 32-row tiles), e.g. under a profiler")
     ap.add_argument("--ref-levels", type=int, default=4, help="time levels per scheme per reference step")
-    ap.add_argument("--profile-case", choices=["k2_tma", "k3_temporal"],
+    ap.add_argument("--profile-case", choices=["k2_tma", "k3_temporal", "kc2_tma"],
                     help="run a short case of one kernel for a profiler capture and exit")
     ap.add_argument("--profile-scheme", type=int, choices=[5, 9, 13], default=13)
+    ap.add_argument("--profile-segment", type=int, default=28, help="derived scheme for kc2_tma")
     args = ap.parse_args()
     if args.profile_case:
-        profile_case(args.profile_case, args.profile_scheme)
+        profile_case(args.profile_case, args.profile_scheme, args.profile_segment)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
