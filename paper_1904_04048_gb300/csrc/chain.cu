@@ -57,15 +57,28 @@ CoefN<V, NC> coef_n(const double* c, double scale = 1.0) {
 
 dim3 grid2d(const wave2d* h) { return dim3((h->nx + 31) / 32, (h->ny + 7) / 8); }
 
-constexpr int kNW = 8;      // warps per CTA of the TMA kernel
-constexpr int kStages = 3;  // pipeline depth
-constexpr int kTH = 32;     // rows per tile
+// Tile shape per storage type and class count: 8 warps on 32-row tiles,
+// 3-stage pipeline, and at most 128 registers so that two CTAs share an SM
+// (the window of 2R + 1 rows stays in registers without spilling for FP32 up
+// to radius 4).  FP32 with eight classes (radius 4) keeps two stages so that
+// two CTAs also fit in shared memory; FP64 with eight classes would spill
+// under the cap and runs one CTA per SM.
+template <typename T, int NC>
+struct ChainTile {
+    static constexpr bool F32 = sizeof(T) == 4;
+    static constexpr int NW = 8;
+    static constexpr int TH = 32;
+    static constexpr int STAGES = (F32 && NC >= 8) ? 2 : 3;
+    static constexpr int MINB = (!F32 && NC >= 8) ? 1 : 2;
+};
 
 template <typename T, int NC, bool PER>
 int launch_tma(wave2d* h) {
+    using Tile = ChainTile<T, NC>;
+    constexpr int kNW = Tile::NW, kTH = Tile::TH;
     using C = ChainTmaCfg<T, NC, kTH, kNW>;
-    auto kern = kc2_tma<T, NC, PER, kTH, kNW, kStages>;
-    const int smem = 2048 + kStages * C::STAGE_BYTES;
+    auto kern = kc2_tma<T, NC, PER, kTH, kNW, Tile::STAGES, Tile::MINB>;
+    const int smem = 2048 + Tile::STAGES * C::STAGE_BYTES;
     static thread_local int configured_smem = -1;  // per instantiation
     if (configured_smem != smem) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -144,15 +157,17 @@ int chain_tma_step(wave2d* h) {
     return rc;
 }
 
-void chain_tma_box(const wave2d* h, int& box_w, int& box_h, int& tile_w) {
+void chain_tma_box(const wave2d* h, int& box_w, int& box_h, int& tile_w, int& tile_h) {
     dispatch_nc(h->nclass, [&](auto NCc) {
         constexpr int NC = decltype(NCc)::value;
         if (h->dtype == DT_F32) {
-            using C = ChainTmaCfg<float, NC, kTH, kNW>;
-            box_w = C::BOX_W, box_h = C::BOX_H, tile_w = C::TW;
+            using Tile = ChainTile<float, NC>;
+            using C = ChainTmaCfg<float, NC, Tile::TH, Tile::NW>;
+            box_w = C::BOX_W, box_h = C::BOX_H, tile_w = C::TW, tile_h = Tile::TH;
         } else {
-            using C = ChainTmaCfg<double, NC, kTH, kNW>;
-            box_w = C::BOX_W, box_h = C::BOX_H, tile_w = C::TW;
+            using Tile = ChainTile<double, NC>;
+            using C = ChainTmaCfg<double, NC, Tile::TH, Tile::NW>;
+            box_w = C::BOX_W, box_h = C::BOX_H, tile_w = C::TW, tile_h = Tile::TH;
         }
     });
 }

@@ -125,8 +125,8 @@ __device__ __forceinline__ ChainRow<T, VEC, H> chain_load_row(const T* row, int 
     return r;
 }
 
-template <typename T, int NC, bool PER, int TH, int NW, int NSTAGES>
-__global__ void __launch_bounds__(NW * 32, 1)
+template <typename T, int NC, bool PER, int TH, int NW, int NSTAGES, int MINB>
+__global__ void __launch_bounds__(NW * 32, MINB)
     kc2_tma(const __grid_constant__ CUtensorMap tm_cur, const __grid_constant__ CUtensorMap tm_prev,
             T* __restrict__ nxt, Geo g, CoefN<T, NC> a, int tiles_x, int n_tiles, int gw, int* status) {
     using C = ChainTmaCfg<T, NC, TH, NW>;

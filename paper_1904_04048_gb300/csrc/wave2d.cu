@@ -205,10 +205,10 @@ static int tma_box(int& bw, int& bh, int& tw) {
 
 static int prepare_tma(wave2d* h) {
     if (h->dtype == DT_F32X2) return set_error(WAVE2D_ERR_ARG, "TMA kernel supports F32 and F64 storage");
-    int bw = 0, bh = 0, tw = 0;
+    int bw = 0, bh = 0, tw = 0, th = 32;
     int rc = WAVE2D_OK;
     if (h->nclass > 0) {
-        chain_tma_box(h, bw, bh, tw);
+        chain_tma_box(h, bw, bh, tw, th);
     } else {
         dispatch_s(h->scheme, [&](auto Sc) {
             constexpr int S = decltype(Sc)::value;
@@ -218,7 +218,7 @@ static int prepare_tma(wave2d* h) {
     }
     for (int p = 0; p < h->nlevels && rc == WAVE2D_OK; ++p) {
         rc = encode_plane(&h->tm_cur[p], h->hi[p], h, bw, bh);
-        if (rc == WAVE2D_OK) rc = encode_plane(&h->tm_prev[p], h->hi[p], h, tw, 32);
+        if (rc == WAVE2D_OK) rc = encode_plane(&h->tm_prev[p], h->hi[p], h, tw, th);
     }
     h->tma_ready = (rc == WAVE2D_OK);
     return rc;
