@@ -176,6 +176,12 @@ __device__ __forceinline__ f2x fma2(f2x a, f2x b, f2x c) {
 // (For the 5-point scheme the last product would feed the addition directly,
 // and a packed multiply followed by a packed add may be fused: that scheme
 // uses the scalar path.)
+// Operand pairs that start at an even column (the centre, the north/south and
+// second-ring neighbours) are register pairs of the row buffers and enter the
+// packed instructions as they are; the east/west and diagonal neighbours of
+// the two nodes start at an odd column, so their pair sums are formed by two
+// scalar additions (the same roundings) whose results make a register pair,
+// instead of moving misaligned operands into pairs first.
 template <int S>
 __device__ __forceinline__ void two_step_update_pair(const float* c, const float* up, const float* dn,
                                                      const float* up2, const float* dn2, int e, float p0,
@@ -184,15 +190,18 @@ __device__ __forceinline__ void two_step_update_pair(const float* c, const float
     static_assert(S == 9 || S == 13, "packed pair path is for the 9- and 13-point schemes");
     const f2x cc = pk2(c[e + 2], c[e + 3]);
     const f2x m4c = mul2(cc, pk2(-4.0f, -4.0f));
-    const f2x d10 = add2(add2(add2(pk2(c[e + 3], c[e + 4]), pk2(c[e + 1], c[e + 2])),
-                              add2(pk2(up[e + 2], up[e + 3]), pk2(dn[e + 2], dn[e + 3]))),
-                         m4c);
+    // delta(1,0): (east + west) + (north + south)
+    const f2x ew = pk2(__fadd_rn(c[e + 3], c[e + 1]), __fadd_rn(c[e + 4], c[e + 2]));
+    const f2x ns = add2(pk2(up[e + 2], up[e + 3]), pk2(dn[e + 2], dn[e + 3]));
+    const f2x d10 = add2(add2(ew, ns), m4c);
     f2x L = mul2(a10, d10);
-    const f2x d11 = add2(add2(add2(pk2(up[e + 3], up[e + 4]), pk2(dn[e + 1], dn[e + 2])),
-                              add2(pk2(up[e + 1], up[e + 2]), pk2(dn[e + 3], dn[e + 4]))),
-                         m4c);
+    // delta(1,1): (ne + sw) + (nw + se)
+    const f2x nesw = pk2(__fadd_rn(up[e + 3], dn[e + 1]), __fadd_rn(up[e + 4], dn[e + 2]));
+    const f2x nwse = pk2(__fadd_rn(up[e + 1], dn[e + 3]), __fadd_rn(up[e + 2], dn[e + 4]));
+    const f2x d11 = add2(add2(nesw, nwse), m4c);
     L = fma2(a11, d11, L);
     if constexpr (S == 13) {
+        // delta(2,0): (ee + ww) + (nn + ss), all pairs even-aligned
         const f2x d20 = add2(add2(add2(pk2(c[e + 4], c[e + 5]), pk2(c[e], c[e + 1])),
                                   add2(pk2(up2[e + 2], up2[e + 3]), pk2(dn2[e + 2], dn2[e + 3]))),
                              m4c);
