@@ -226,7 +226,10 @@ static int prepare_tma(wave2d* h) {
 
 // Temporal kernel: region width in vectors and warps per CTA.
 constexpr int kTempRVW = 64;
-constexpr int kTempNW = 8;
+// Warps per CTA: 8 for tiles of 16, 24 or 32 rows (two or three CTAs share
+// an SM), 16 for 64-row tiles (one CTA of 160 KB per SM, 16 warps).
+template <int OH>
+constexpr int temp_nw() { return OH == 64 ? 16 : 8; }
 
 static int prepare_temporal(wave2d* h) {
     const int key = h->scheme * 10000 + h->temporal_oh * 10 + h->temporal_t;
@@ -394,6 +397,7 @@ static int launch_tma_step(wave2d* h) {
 template <int S, bool PER, int OH, int T>
 static int launch_temporal_t(wave2d* h) {
     using C = TemporalCfg<S, kTempRVW, OH, T>;
+    constexpr int kTempNW = temp_nw<OH>();
     auto kern = k3_temporal<S, PER, kTempRVW, OH, T, kTempNW>;
     const int smem = 1024 + 2 * C::BUF_BYTES;
     static thread_local bool configured = false;  // per instantiation
@@ -423,10 +427,17 @@ static int launch_temporal(wave2d* h) {
         dispatch_bool(h->bc == WAVE2D_BC_PERIODIC, [&](auto Pc) {
             constexpr bool P = decltype(Pc)::value;
             const int T = h->temporal_t, OH = h->temporal_oh;
-            if (T == 2 && OH == 32) rc = launch_temporal_t<S, P, 32, 2>(h);
-            else if (T == 2) rc = launch_temporal_t<S, P, 64, 2>(h);
-            else if (OH == 32) rc = launch_temporal_t<S, P, 32, 4>(h);
-            else rc = launch_temporal_t<S, P, 64, 4>(h);
+            auto by_oh = [&](auto Tc) {
+                constexpr int TT = decltype(Tc)::value;
+                switch (OH) {
+                    case 16: rc = launch_temporal_t<S, P, 16, TT>(h); break;
+                    case 24: rc = launch_temporal_t<S, P, 24, TT>(h); break;
+                    case 64: rc = launch_temporal_t<S, P, 64, TT>(h); break;
+                    default: rc = launch_temporal_t<S, P, 32, TT>(h); break;
+                }
+            };
+            if (T == 2) by_oh(IC<2>{});
+            else by_oh(IC<4>{});
         });
     });
     return rc;
@@ -490,7 +501,7 @@ static int select_kernel(wave2d* h) {
     }
     if (want == WAVE2D_KERNEL_TEMPORAL) {
         h->temporal_t = h->tune.temporal_t > 0 ? h->tune.temporal_t : 4;
-        h->temporal_oh = h->tune.tile_h > 0 ? h->tune.tile_h : 64;
+        h->temporal_oh = h->tune.tile_h > 0 ? h->tune.tile_h : 32;
         int rc = prepare_temporal(h);
         if (rc != WAVE2D_OK) return rc;
     }
@@ -805,6 +816,12 @@ int wave2d_set_tuning(wave2d_t h, const wave2d_tune* tune) {
         return set_error(WAVE2D_ERR_ARG, "the TMA kernel supports F32 and F64 storage only");
     if (tune->kernel == WAVE2D_KERNEL_TEMPORAL && h->nclass > 0)
         return set_error(WAVE2D_ERR_ARG, "the temporal kernel covers the 5-, 9- and 13-point schemes only");
+    if (tune->kernel == WAVE2D_KERNEL_TEMPORAL &&
+        !(tune->temporal_t == 0 || tune->temporal_t == 2 || tune->temporal_t == 4))
+        return set_error(WAVE2D_ERR_ARG, "temporal_t must be 0 (auto), 2 or 4 (got %d)", tune->temporal_t);
+    if (tune->kernel == WAVE2D_KERNEL_TEMPORAL && !(tune->tile_h == 0 || tune->tile_h == 16 ||
+                                                    tune->tile_h == 24 || tune->tile_h == 32 || tune->tile_h == 64))
+        return set_error(WAVE2D_ERR_ARG, "temporal tile_h must be 0 (auto), 16, 24, 32 or 64 (got %d)", tune->tile_h);
     if (tune->ctas_per_sm < 0 || tune->ctas_per_sm > 32)
         return set_error(WAVE2D_ERR_ARG, "ctas_per_sm must be 0 (auto) or 1..32");
     h->tune = *tune;
@@ -1090,7 +1107,7 @@ int wave2d_autotune(wave2d_t h, int64_t steps, wave2d_tune* best) {
         add(WAVE2D_KERNEL_TMA, 0, 0, 1);
         add(WAVE2D_KERNEL_TMA, 0, 0, 2);
         for (int T : {2, 4})
-            for (int oh : {32, 64}) add(WAVE2D_KERNEL_TEMPORAL, oh, T, 0);
+            for (int oh : {16, 24, 32, 64}) add(WAVE2D_KERNEL_TEMPORAL, oh, T, 0);
     } else if (h->dtype == WAVE2D_F64) {
         add(WAVE2D_KERNEL_TMA, 0, 0, 1);
         add(WAVE2D_KERNEL_TMA, 0, 0, 2);
