@@ -50,10 +50,15 @@ FP32_OPS = {5: 9, 9: 14, 13: 19}
 
 # DRAM bytes (read + write) of one launch of a kernel at the benchmark size,
 # from an ncu capture of the same kernel source (see the profiles directory),
-# keyed by (kernel, hash of the kernel sources) so that a figure is dropped
-# once the kernel changes.
-NCU_TRAFFIC = {("k3_temporal", "9651de351bb6011b"): 136013056 + 89094144,
-               ("k2_tma", "9651de351bb6011b"): 135365888 + 20342784}
+# keyed by (kernel, hash of the kernel sources, scheme, tile rows) so that a
+# figure is dropped once the kernel or the autotuner's choice changes.
+NCU_TRAFFIC = {("k3_temporal", "92440fad3f09d537", 13, 32): 136017664 + 88732160,
+               ("k3_temporal", "92440fad3f09d537", 9, 24): 135961600 + 87288320,
+               ("k2_tma", "92440fad3f09d537", 13, 0): 135368192 + 20378880}
+
+# The autotuner's choice on GB300 (temporal kernel, T = 4, rows per tile),
+# used by --fixed-tuning for profiler runs.
+FIXED_TILE = {9: 24, 13: 32}
 
 
 def kernel_source_hash() -> str:
@@ -204,8 +209,8 @@ def run_ours(args, rank, world, local_rank):
     for s in SCHEMES:
         sims[s].first_step(du0, dv0)
         if args.fixed_tuning:  # the autotuner's choice on the measured runs
-            sims[s].set_tuning(kernel=w.KERNEL_TEMPORAL, temporal_t=4, tile_h=32)
-            best = w.wave2d_tune(w.KERNEL_TEMPORAL, 32, 4, -1, 0)
+            sims[s].set_tuning(kernel=w.KERNEL_TEMPORAL, temporal_t=4, tile_h=FIXED_TILE[s])
+            best = w.wave2d_tune(w.KERNEL_TEMPORAL, FIXED_TILE[s], 4, -1, 0)
         else:
             best = sims[s].autotune(steps=64)
         tuned[s] = {"kernel": {1: "simple", 2: "tma", 3: "temporal"}[best.kernel],
@@ -325,7 +330,11 @@ def run_ours(args, rank, world, local_rank):
         kname = "k2_tma (two-step, FP32, 9/13-point)"
         effective = alg_bytes / avg_launch / 1e9
     achieved = alg_bytes / avg_launch / 1e9
-    traffic = NCU_TRAFFIC.get((kname.split()[0], src_hash))
+    if kernel == w.KERNEL_TEMPORAL:
+        per = [NCU_TRAFFIC.get(("k3_temporal", src_hash, s, tuned[s]["tile_h"])) for s in SCHEMES]
+    else:
+        per = [NCU_TRAFFIC.get(("k2_tma", src_hash, s, 0)) for s in SCHEMES]
+    traffic = int(sum(per) / len(per)) if all(per) else None  # mean over the schemes' launches
     clocks = clk.summary()
     hbm_view = {"bound": "hbm", "kernel": kname, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "peak_source": peak_src,
@@ -371,7 +380,7 @@ def run_ours(args, rank, world, local_rank):
         "one_step_kernel": ({"kernel": "k2_tma", "avg_launch_us": {str(s): round(one_step[s] * 1e6, 3) for s in SCHEMES},
                              "frac": {str(s): round(12 * N * N / one_step[s] / 1e9 / peak, 4) for s in SCHEMES},
                              "algorithmic_bytes_per_launch": 12 * N * N,
-                             "traffic": NCU_TRAFFIC.get(("k2_tma", src_hash))}
+                             "traffic": NCU_TRAFFIC.get(("k2_tma", src_hash, 13, 0))}
                             if all(one_step[s] for s in SCHEMES) else None),
         "clocks": clocks,
         "result_norms": {str(s): [results[s][0], results[s][1]] for s in SCHEMES},
@@ -381,6 +390,7 @@ def run_ours(args, rank, world, local_rank):
         line["batched"] = measure_batched(w, torch)
         line["served"] = measure_served(w, torch)
         line["derived_schemes"] = measure_derived(w, torch, u0, v0, peak)
+        line["fp32_difference_sums"] = measure_diff_sums(w, torch, u0, v0, peak)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = time_oracle(u0, v0, args.cpu_budget)
     return line
@@ -562,13 +572,42 @@ def measure_derived(w, torch, u0, v0, peak):
     return out
 
 
-def profile_case(kernel: str, scheme: int, segment: int = 28):
+def measure_diff_sums(w, torch, u0, v0, peak):
+    """The 9- and 13-point schemes with WAVE2D_DIFF_SUMS (stencil sums from
+    differences to the centre, FP32) on the benchmark grid and inputs:
+    autotuned two-step kernel, 200 levels timed with CUDA events after 20
+    warm-up levels; HBM roofline at 12 B per node-update."""
+    from initial_data import BC_PERIODIC, LAMBDA_MAX
+    out = {}
+    h = 1.0 / N
+    for scheme in SCHEMES:
+        lam = 0.9 * LAMBDA_MAX[scheme]
+        stream = torch.cuda.Stream()
+        with w.Wave2D(N, N, h, lam * h, scheme=scheme, bc=BC_PERIODIC, dtype=w.F32, flags=w.DIFF_SUMS,
+                      stream=stream.cuda_stream) as sim:
+            sim.first_step(u0, v0)
+            best = sim.autotune(steps=16)
+            sim.step_n(20)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            levels = 200
+            e0.record(stream)
+            sim.step_n(levels)
+            e1.record(stream)
+            e1.synchronize()
+            sec = e0.elapsed_time(e1) / 1e3 / levels
+        out[str(scheme)] = {"us_per_level": round(sec * 1e6, 2), "value": round(N * N / sec / 1e9, 1),
+                            "unit": "G point-updates/s", "kernel": {1: "simple", 2: "tma", 3: "temporal"}.get(best.kernel),
+                            "hbm_frac": round(12 * N * N / sec / 1e9 / peak, 3)}
+    return out
+
+
+def profile_case(kernel: str, scheme: int, segment: int = 28, tile_h: int = 32):
     """A short run of one kernel at the benchmark size, for profiler captures:
     the first step, then a few launches of the named kernel on the
     benchmark's inputs (no timing, no JSON line).  4096^2 FP32 holds about
     0.5 GB on the device.
       k2_tma:      4 one-step launches (the first step comes before them)
-      k3_temporal: 3 launches of T = 4 levels, 32-row tiles
+      k3_temporal: 3 launches of T = 4 levels, tile_h-row tiles
       kc2_tma:     4 one-step launches of a derived scheme (``segment``)"""
     from initial_data import BC_PERIODIC, LAMBDA_MAX, pulses_and_noise
     from paper_1904_04048_gb300 import wave2d as w
@@ -584,7 +623,7 @@ def profile_case(kernel: str, scheme: int, segment: int = 28):
             sim.set_tuning(kernel=w.KERNEL_TMA, use_graph=0)
             levels = 4
         else:
-            sim.set_tuning(kernel=w.KERNEL_TEMPORAL, temporal_t=4, tile_h=32, use_graph=0)
+            sim.set_tuning(kernel=w.KERNEL_TEMPORAL, temporal_t=4, tile_h=tile_h, use_graph=0)
             levels = 12
         sim.first_step(u0, v0)
         sim.step_n(levels)
@@ -638,15 +677,16 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the batched and served workloads")
     ap.add_argument("--fixed-tuning", action="store_true",
-                    help="skip the autotuner (temporal kernel, T = 4, 32-row tiles), e.g. under a profiler")
+                    help="skip the autotuner (temporal kernel, T = 4, the tiles of FIXED_TILE), e.g. under a profiler")
     ap.add_argument("--ref-levels", type=int, default=4, help="time levels per scheme per reference step")
     ap.add_argument("--profile-case", choices=["k2_tma", "k3_temporal", "kc2_tma"],
                     help="run a short case of one kernel for a profiler capture and exit")
     ap.add_argument("--profile-scheme", type=int, choices=[5, 9, 13], default=13)
     ap.add_argument("--profile-segment", type=int, default=28, help="derived scheme for kc2_tma")
+    ap.add_argument("--profile-tile", type=int, default=32, help="rows per tile for k3_temporal")
     args = ap.parse_args()
     if args.profile_case:
-        profile_case(args.profile_case, args.profile_scheme, args.profile_segment)
+        profile_case(args.profile_case, args.profile_scheme, args.profile_segment, args.profile_tile)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -467,7 +467,8 @@ int wave2d_batch_create(wave2d_t* handles, int n, const wave2d_tune* opt, wave2d
         if (!handles[i]) return set_error(WAVE2D_ERR_ARG, "null handle %d", i);
         if (handles[i]->dtype != WAVE2D_F32) return set_error(WAVE2D_ERR_ARG, "batched stepping needs F32 storage");
         if (handles[i]->nclass > 0)
-            return set_error(WAVE2D_ERR_ARG, "batched stepping covers the 5-, 9- and 13-point schemes only");
+            return set_error(WAVE2D_ERR_ARG,
+                             "batched stepping covers the 5-, 9- and 13-point schemes with plain sums only");
         if (handles[i]->bc != handles[0]->bc) return set_error(WAVE2D_ERR_ARG, "all handles of a batch share one boundary");
         if (handles[i]->device != handles[0]->device) return set_error(WAVE2D_ERR_ARG, "all handles of a batch share one device");
         for (int j = 0; j < i; ++j)

@@ -5,6 +5,8 @@
 //   kc1_first_step  first time step, Eq. A1, FP64 math, one node per thread
 //   kc2_simple      two-step, Eq. A2, one node per thread (any storage type),
 //                   optional fused space-time error reduction
+//   (the two-step kernels also come with the difference sums of
+//   stencil_chain.cuh, DIFF = true, for FP32 and FP64 storage)
 //   kc2_tma         two-step through TMA-staged tiles (F32 / F64 storage):
 //                   persistent CTAs, NSTAGES-deep mbarrier pipeline, each lane
 //                   walks down one column vector keeping 2R + 1 rows in
@@ -46,7 +48,7 @@ __global__ void __launch_bounds__(256) kc1_first_step(const double* __restrict__
     if (TRACK) reduce_finalize<256>(s0, s1, m0, m1, rd);
 }
 
-template <int DT, int NC, bool PER, bool TRACK>
+template <int DT, int NC, bool PER, bool TRACK, bool DIFF>
 __global__ void __launch_bounds__(256) kc2_simple(Level cur, Level nxt, Geo g,
                                                   CoefN<typename St<DT>::V, NC> a, ExactTab ex,
                                                   Reduce rd, int gw) {
@@ -59,7 +61,7 @@ __global__ void __launch_bounds__(256) kc2_simple(Level cur, Level nxt, Geo g,
         const size_t o = off(g, i, j);
         const long long P = g.pitch;
         const auto u = [&](int dx, int dy) { return T::ldg(cur, (size_t)((long long)o + dy * P + dx)); };
-        const V r = two_step_chain<NC>(u, u(0, 0), T::ld(nxt, o), a);
+        const V r = two_step_chain<NC, DIFF>(u, u(0, 0), T::ld(nxt, o), a);
         T::st(nxt, o, r);
         if (PER) write_images<DT>(nxt, g, i, j, r, gw);
         if (TRACK) error_terms(T::to_d(r), exact_at(ex, i, j), s0, s1, m0, m1, rd.status);
@@ -125,7 +127,7 @@ __device__ __forceinline__ ChainRow<T, VEC, H> chain_load_row(const T* row, int 
     return r;
 }
 
-template <typename T, int NC, bool PER, int TH, int NW, int NSTAGES, int MINB>
+template <typename T, int NC, bool PER, int TH, int NW, int NSTAGES, int MINB, bool DIFF>
 __global__ void __launch_bounds__(NW * 32, MINB)
     kc2_tma(const __grid_constant__ CUtensorMap tm_cur, const __grid_constant__ CUtensorMap tm_prev,
             T* __restrict__ nxt, Geo g, CoefN<T, NC> a, int tiles_x, int n_tiles, int gw, int* status) {
@@ -203,7 +205,7 @@ __global__ void __launch_bounds__(NW * 32, MINB)
 #pragma unroll
             for (int e = 0; e < VEC; ++e) {
                 const auto u = [&](int dx, int dy) -> T { return win[R + dy].a[H + e + dx]; };
-                out[e] = two_step_chain<NC>(u, u(0, 0), pv[e], a);
+                out[e] = two_step_chain<NC, DIFF>(u, u(0, 0), pv[e], a);
             }
             const int y = ty * TH + r0 + r;
             if (y < g.ny) {

@@ -335,6 +335,8 @@ int wave2d_server_submit(wave2d_server_t s, const wave2d_request* r) {
     if (r->nx < 1 || r->ny < 1 || r->steps < 0 || (r->scheme != 5 && r->scheme != 9 && r->scheme != 13))
         return set_error(WAVE2D_ERR_ARG, "invalid request");
     if ((r->u0 == nullptr) != (r->v0 == nullptr)) return set_error(WAVE2D_ERR_ARG, "u0 and v0 go together");
+    if (r->flags & ~(WAVE2D_ALLOW_UNSTABLE | WAVE2D_CONVENTIONAL))
+        return set_error(WAVE2D_ERR_ARG, "request flags may hold WAVE2D_ALLOW_UNSTABLE and WAVE2D_CONVENTIONAL only");
     const double lam = r->c * r->tau / r->h;
     if (!(lam > 0) || (lam > wave2d_lambda_max(r->scheme, (r->flags & WAVE2D_CONVENTIONAL) != 0) * (1 + 1e-12) &&
                        !(r->flags & WAVE2D_ALLOW_UNSTABLE)))

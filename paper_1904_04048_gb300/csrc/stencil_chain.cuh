@@ -19,6 +19,15 @@
 // operands of commutative additions and the result is equivariant bit for
 // bit.  For NC <= 3 the operations are exactly those of the Section 6
 // schemes in stencil_ops.cuh, in the same order.
+//
+// Difference sums (DIFF = true): each node enters as its difference to the
+// centre, delta_c = ((u_q - u_ij) + (u_-q - u_ij)) + ((u_r - u_ij) + (u_-r - u_ij)).
+// For a smooth field, away from its zeros, a neighbour and the centre are
+// within a factor two of each other, so each difference is exact (Sterbenz's
+// lemma) and the rounding error of delta is relative to delta itself, not to
+// u: for long
+// waves (delta ~ (omega tau)^2 u) this keeps the bits the plain sum loses to
+// cancellation.  Same pairing, so the same bitwise symmetry.
 #pragma once
 #include "stencil_ops.cuh"
 
@@ -55,36 +64,46 @@ struct CoefN {
 
 // delta_c of class C at a node; u(dx, dy) returns the level at offset
 // (dx, dy) (dx along x1 = columns, dy along x2 = rows).
-template <int C, typename V, typename F>
+template <int C, bool DIFF, typename V, typename F>
 __device__ __forceinline__ V class_delta(const F& u, V c) {
     constexpr int q1 = chain_q1(C), q2 = chain_q2(C);
-    V s = vadd(vadd(u(q1, q2), u(-q1, -q2)), vadd(u(-q2, q1), u(q2, -q1)));
-    if constexpr (chain_nodes(C) == 8) {
-        const V t = vadd(vadd(u(q2, q1), u(-q2, -q1)), vadd(u(-q1, q2), u(q1, -q2)));
-        s = vadd(s, t);
+    if constexpr (DIFF) {
+        const auto d = [&](int x, int y) { return vsub(u(x, y), c); };
+        V s = vadd(vadd(d(q1, q2), d(-q1, -q2)), vadd(d(-q2, q1), d(q2, -q1)));
+        if constexpr (chain_nodes(C) == 8) {
+            const V t = vadd(vadd(d(q2, q1), d(-q2, -q1)), vadd(d(-q1, q2), d(q1, -q2)));
+            s = vadd(s, t);
+        }
+        return s;
+    } else {
+        V s = vadd(vadd(u(q1, q2), u(-q1, -q2)), vadd(u(-q2, q1), u(q2, -q1)));
+        if constexpr (chain_nodes(C) == 8) {
+            const V t = vadd(vadd(u(q2, q1), u(-q2, -q1)), vadd(u(-q1, q2), u(q1, -q2)));
+            s = vadd(s, t);
+        }
+        return vadd(s, vscale(c, -(float)chain_nodes(C)));
     }
-    return vadd(s, vscale(c, -(float)chain_nodes(C)));
 }
 
-template <int NC, typename V, typename F>
+template <int NC, bool DIFF = false, typename V, typename F>
 __device__ __forceinline__ V lambda_chain(const F& u, V c, const CoefN<V, NC>& a) {
     static_assert(NC >= 1 && NC <= kMaxClasses, "class count");
-    V L = vmul(a.a[0], class_delta<0>(u, c));
-    if constexpr (NC > 1) L = vfma(a.a[1], class_delta<1>(u, c), L);
-    if constexpr (NC > 2) L = vfma(a.a[2], class_delta<2>(u, c), L);
-    if constexpr (NC > 3) L = vfma(a.a[3], class_delta<3>(u, c), L);
-    if constexpr (NC > 4) L = vfma(a.a[4], class_delta<4>(u, c), L);
-    if constexpr (NC > 5) L = vfma(a.a[5], class_delta<5>(u, c), L);
-    if constexpr (NC > 6) L = vfma(a.a[6], class_delta<6>(u, c), L);
-    if constexpr (NC > 7) L = vfma(a.a[7], class_delta<7>(u, c), L);
+    V L = vmul(a.a[0], class_delta<0, DIFF>(u, c));
+    if constexpr (NC > 1) L = vfma(a.a[1], class_delta<1, DIFF>(u, c), L);
+    if constexpr (NC > 2) L = vfma(a.a[2], class_delta<2, DIFF>(u, c), L);
+    if constexpr (NC > 3) L = vfma(a.a[3], class_delta<3, DIFF>(u, c), L);
+    if constexpr (NC > 4) L = vfma(a.a[4], class_delta<4, DIFF>(u, c), L);
+    if constexpr (NC > 5) L = vfma(a.a[5], class_delta<5, DIFF>(u, c), L);
+    if constexpr (NC > 6) L = vfma(a.a[6], class_delta<6, DIFF>(u, c), L);
+    if constexpr (NC > 7) L = vfma(a.a[7], class_delta<7, DIFF>(u, c), L);
     return L;
 }
 
 // Two-step (Eq. A2): (2u^k - u^{k-1}) + Lambda_a(u^k), Lambda accumulated on
 // its own and added once (the order of two_step_update).
-template <int NC, typename V, typename F>
+template <int NC, bool DIFF = false, typename V, typename F>
 __device__ __forceinline__ V two_step_chain(const F& u, V c, V prev, const CoefN<V, NC>& a) {
-    const V L = lambda_chain<NC>(u, c, a);
+    const V L = lambda_chain<NC, DIFF>(u, c, a);
     const V base = vsub(vscale(c, 2.0f), prev);
     return vadd(base, L);
 }

@@ -659,6 +659,8 @@ static int check_grid(const wave2d_grid* grid, double hh, double tau, double c, 
     if (grid->dtype != WAVE2D_F64 && grid->dtype != WAVE2D_F32 && grid->dtype != WAVE2D_F32X2)
         return set_error(WAVE2D_ERR_ARG, "unknown dtype %d", grid->dtype);
     if (grid->flags & ~allowed_flags) return set_error(WAVE2D_ERR_ARG, "unsupported flags 0x%x", grid->flags);
+    if ((grid->flags & WAVE2D_DIFF_SUMS) && grid->dtype == WAVE2D_F32X2)
+        return set_error(WAVE2D_ERR_ARG, "difference sums are available for F32 and F64 storage");
     if (!(hh > 0) || !(tau > 0) || !(c > 0) || !std::isfinite(hh) || !std::isfinite(tau) || !std::isfinite(c))
         return set_error(WAVE2D_ERR_ARG, "h, tau and c must be positive and finite");
     return WAVE2D_OK;
@@ -740,7 +742,7 @@ int wave2d_create(const wave2d_grid* grid, double hh, double tau, double c, int 
     *out = nullptr;
     if (scheme != 5 && scheme != 9 && scheme != 13)
         return set_error(WAVE2D_ERR_ARG, "scheme must be 5, 9 or 13 (got %d)", scheme);
-    int rc = check_grid(grid, hh, tau, c, WAVE2D_ALLOW_UNSTABLE | WAVE2D_CONVENTIONAL);
+    int rc = check_grid(grid, hh, tau, c, WAVE2D_ALLOW_UNSTABLE | WAVE2D_CONVENTIONAL | WAVE2D_DIFF_SUMS);
     if (rc != WAVE2D_OK) return rc;
     const bool conventional = (grid->flags & WAVE2D_CONVENTIONAL) != 0;
     const double lam = c * tau / hh;
@@ -757,6 +759,16 @@ int wave2d_create(const wave2d_grid* grid, double hh, double tau, double c, int 
     h->npoints = scheme;
     h->lam_max = lmax;
     scheme_coefficients(scheme, conventional, lam, h->a, h->b);
+    if (grid->flags & WAVE2D_DIFF_SUMS) {
+        // The class-chain kernels carry the difference sums: the Section 6
+        // scheme is its first one, two or three classes.
+        h->diff_sums = true;
+        h->nclass = scheme == 5 ? 1 : scheme == 9 ? 2 : 3;
+        for (int q = 0; q < 3; ++q) {
+            h->ca[q] = h->a[q];
+            h->cb[q] = h->b[q];
+        }
+    }
     rc = create_device_state(h, grid);
     if (rc != WAVE2D_OK) {
         release_handle(h);
@@ -773,7 +785,7 @@ int wave2d_create_scheme(const wave2d_grid* grid, double hh, double tau, double 
     *out = nullptr;
     int rc = check_scheme(s);
     if (rc != WAVE2D_OK) return rc;
-    rc = check_grid(grid, hh, tau, c, WAVE2D_ALLOW_UNSTABLE);
+    rc = check_grid(grid, hh, tau, c, WAVE2D_ALLOW_UNSTABLE | WAVE2D_DIFF_SUMS);
     if (rc != WAVE2D_OK) return rc;
     const double lam = c * tau / hh;
     const double lmax = scheme_lambda_max(s);
@@ -784,6 +796,7 @@ int wave2d_create_scheme(const wave2d_grid* grid, double hh, double tau, double 
     if (!h) return set_error(WAVE2D_ERR_OOM, "host allocation failed");
     set_problem(h, grid, hh, tau, c);
     h->scheme = 0;
+    h->diff_sums = (grid->flags & WAVE2D_DIFF_SUMS) != 0;
     h->nclass = s->n_classes;
     h->R = chain_radius(s->n_classes);
     h->npoints = chain_points(s->n_classes);
@@ -815,7 +828,8 @@ int wave2d_set_tuning(wave2d_t h, const wave2d_tune* tune) {
     if (tune->kernel == WAVE2D_KERNEL_TMA && h->dtype == WAVE2D_F32X2)
         return set_error(WAVE2D_ERR_ARG, "the TMA kernel supports F32 and F64 storage only");
     if (tune->kernel == WAVE2D_KERNEL_TEMPORAL && h->nclass > 0)
-        return set_error(WAVE2D_ERR_ARG, "the temporal kernel covers the 5-, 9- and 13-point schemes only");
+        return set_error(WAVE2D_ERR_ARG,
+                         "the temporal kernel covers the 5-, 9- and 13-point schemes with plain sums only");
     if (tune->kernel == WAVE2D_KERNEL_TEMPORAL &&
         !(tune->temporal_t == 0 || tune->temporal_t == 2 || tune->temporal_t == 4))
         return set_error(WAVE2D_ERR_ARG, "temporal_t must be 0 (auto), 2 or 4 (got %d)", tune->temporal_t);

@@ -66,6 +66,7 @@ struct wave2d {
     // Section 6 schemes), stencil nodes, and the class coefficients at lambda
     int nclass = 0, npoints = 0;
     double ca[8] = {}, cb[8] = {};
+    bool diff_sums = false;  // WAVE2D_DIFF_SUMS: class sums from differences to the centre
     // device
     int device = 0, num_sms = 0, l2_bytes = 0;
     cudaStream_t stream = nullptr;
@@ -114,8 +115,8 @@ struct wave2d {
 };
 
 namespace w2d {
-// Derived schemes (chain.cu): launches of the class-chain kernels for a
-// handle with nclass > 0.
+// Derived schemes and difference sums (chain.cu, chain_tma.cu): launches of
+// the class-chain kernels for a handle with nclass > 0.
 int chain_first_step(wave2d* h, const double* du0, const double* dv0, const ExactTab& ex, const Reduce& rd);
 int chain_simple_step(wave2d* h, bool track, const ExactTab& ex, const Reduce& rd);
 int chain_tma_step(wave2d* h);
