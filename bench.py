@@ -573,17 +573,21 @@ def measure_derived(w, torch, u0, v0, peak):
 
 
 def measure_diff_sums(w, torch, u0, v0, peak):
-    """The 9- and 13-point schemes with WAVE2D_DIFF_SUMS (stencil sums from
-    differences to the centre, FP32) on the benchmark grid and inputs:
-    autotuned two-step kernel, 200 levels timed with CUDA events after 20
-    warm-up levels; HBM roofline at 12 B per node-update."""
+    """The 9- and 13-point schemes in FP32 with WAVE2D_DIFF_SUMS (stencil sums
+    from differences to the centre; 12 B per node-update) and with
+    WAVE2D_DIFF_FORM (levels kept as u^k and d^k = u^k - u^{k-1}; 16 B per
+    node-update) on the benchmark grid and inputs: autotuned two-step kernel,
+    200 levels timed with CUDA events after 20 warm-up levels; HBM roofline
+    at the algorithmic bytes."""
     from initial_data import BC_PERIODIC, LAMBDA_MAX
     out = {}
     h = 1.0 / N
-    for scheme in SCHEMES:
+    cases = [(name, flags, bpn, scheme) for (name, flags, bpn) in (("sums", w.DIFF_SUMS, 12), ("form", w.DIFF_FORM, 16))
+             for scheme in SCHEMES]
+    for name, flags, bpn, scheme in cases:
         lam = 0.9 * LAMBDA_MAX[scheme]
         stream = torch.cuda.Stream()
-        with w.Wave2D(N, N, h, lam * h, scheme=scheme, bc=BC_PERIODIC, dtype=w.F32, flags=w.DIFF_SUMS,
+        with w.Wave2D(N, N, h, lam * h, scheme=scheme, bc=BC_PERIODIC, dtype=w.F32, flags=flags,
                       stream=stream.cuda_stream) as sim:
             sim.first_step(u0, v0)
             best = sim.autotune(steps=16)
@@ -595,9 +599,11 @@ def measure_diff_sums(w, torch, u0, v0, peak):
             e1.record(stream)
             e1.synchronize()
             sec = e0.elapsed_time(e1) / 1e3 / levels
-        out[str(scheme)] = {"us_per_level": round(sec * 1e6, 2), "value": round(N * N / sec / 1e9, 1),
-                            "unit": "G point-updates/s", "kernel": {1: "simple", 2: "tma", 3: "temporal"}.get(best.kernel),
-                            "hbm_frac": round(12 * N * N / sec / 1e9 / peak, 3)}
+        out[f"{name}_{scheme}"] = {"us_per_level": round(sec * 1e6, 2), "value": round(N * N / sec / 1e9, 1),
+                                   "unit": "G point-updates/s",
+                                   "kernel": {1: "simple", 2: "tma", 3: "temporal"}.get(best.kernel),
+                                   "bytes_per_node_update": bpn,
+                                   "hbm_frac": round(bpn * N * N / sec / 1e9 / peak, 3)}
     return out
 
 

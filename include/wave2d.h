@@ -79,12 +79,23 @@ enum {
     WAVE2D_ALLOW_UNSTABLE = 1, /* accept lambda > lambda_max (for instability tests) */
     WAVE2D_CONVENTIONAL = 2,   /* comparison schemes: central-difference first step,
                                   isotropic 9-point Laplacian (Eq. comp9.2b)        */
-    WAVE2D_DIFF_SUMS = 4       /* form each stencil sum of the two-step from the
+    WAVE2D_DIFF_SUMS = 4,      /* form each stencil sum of the two-step from the
                                   differences u_q - u_ij (exact for neighbouring
-                                  values of a smooth field): the same operator,
-                                  far less cancellation for long waves in FP32.
-                                  F32 and F64 storage; one-node and TMA kernels
-                                  only (no temporal blocking, no batches).        */
+                                  values of a smooth field): the same operator
+                                  with less cancellation in the sums (measured
+                                  3-4x lower FP32 error for mid-length waves; the
+                                  longest waves need WAVE2D_DIFF_FORM).  F32 and
+                                  F64 storage; one-node and TMA kernels only (no
+                                  temporal blocking, no batches).                */
+    WAVE2D_DIFF_FORM = 8       /* F32 only: keep u^k and d^k = u^k - u^{k-1} and
+                                  step d^{k+1} = d^k + Lambda(u^k),
+                                  u^{k+1} = u^k + d^{k+1} (the same recursion,
+                                  Eq. A2) with difference sums: the rounding of
+                                  u enters once instead of being integrated
+                                  twice.  Three planes, 16 B per node-update;
+                                  one-node and TMA kernels.  get/set_state
+                                  convert to and from (u^{k-1}, u^k) in FP64;
+                                  the raw layout is [d^k][u^k].                 */
 };
 
 /* Exact solutions for wave2d_error_vs_exact / wave2d_track_error.
@@ -109,7 +120,8 @@ typedef struct {
     int32_t nx, ny; /* updated nodes along x1 and x2 (1 .. 65536 each)          */
     int32_t bc;     /* WAVE2D_BC_*                                             */
     int32_t dtype;  /* WAVE2D_F64 | WAVE2D_F32 | WAVE2D_F32X2                  */
-    int32_t flags;  /* WAVE2D_ALLOW_UNSTABLE | WAVE2D_CONVENTIONAL | WAVE2D_DIFF_SUMS */
+    int32_t flags;  /* WAVE2D_ALLOW_UNSTABLE | WAVE2D_CONVENTIONAL | WAVE2D_DIFF_SUMS |
+                       WAVE2D_DIFF_FORM                                         */
     int32_t reserved;
     void *stream;   /* cudaStream_t the handle launches on; NULL = default stream */
 } wave2d_grid;
@@ -225,8 +237,8 @@ int wave2d_scheme_lambda_max(const wave2d_scheme *s, double *out);
  * wave2d_create.  The coefficients are evaluated at lambda = c tau / h in
  * FP64.  The two-step runs on the one-node kernel or the TMA kernel
  * (WAVE2D_KERNEL_TEMPORAL is not available: WAVE2D_ERR_ARG from
- * wave2d_set_tuning); grid.flags may hold WAVE2D_ALLOW_UNSTABLE and
- * WAVE2D_DIFF_SUMS, not WAVE2D_CONVENTIONAL.  Errors as
+ * wave2d_set_tuning); grid.flags may hold WAVE2D_ALLOW_UNSTABLE,
+ * WAVE2D_DIFF_SUMS and WAVE2D_DIFF_FORM, not WAVE2D_CONVENTIONAL.  Errors as
  * wave2d_create, with the stability limit of wave2d_scheme_lambda_max. */
 int wave2d_create_scheme(const wave2d_grid *grid, double h, double tau, double c,
                          const wave2d_scheme *s, wave2d_t *out);

@@ -20,12 +20,12 @@ struct ChainTile {
     static constexpr int MINB = (!F32 && NC >= 8) ? 1 : 2;
 };
 
-template <typename T, int NC, bool PER, bool DIFF>
+template <typename T, int NC, bool PER, bool DIFF, bool DFORM>
 int launch_tma(wave2d* h) {
     using Tile = ChainTile<T, NC>;
     constexpr int kNW = Tile::NW, kTH = Tile::TH;
     using C = ChainTmaCfg<T, NC, kTH, kNW>;
-    auto kern = kc2_tma<T, NC, PER, kTH, kNW, Tile::STAGES, Tile::MINB, DIFF>;
+    auto kern = kc2_tma<T, NC, PER, kTH, kNW, Tile::STAGES, Tile::MINB, DIFF, DFORM>;
     const int smem = 2048 + Tile::STAGES * C::STAGE_BYTES;
     static thread_local int configured_smem = -1;  // per instantiation
     if (configured_smem != smem) {
@@ -45,9 +45,12 @@ int launch_tma(wave2d* h) {
     if (per_sm <= 0) per_sm = (2.0 * (double)h->plane_bytes <= 1.25 * (double)h->l2_bytes) ? occ : 1;
     per_sm = std::max(1, std::min(per_sm, occ));
     const int grid = std::min(n_tiles, per_sm * h->num_sms);
-    kern<<<grid, kNW * 32, smem, h->stream>>>(h->tm_cur[h->cur], h->tm_prev[h->prv],
+    // difference form: the second staged box is d^k (plane 2), updated in place
+    const int second = DFORM ? 2 : h->prv;
+    kern<<<grid, kNW * 32, smem, h->stream>>>(h->tm_cur[h->cur], h->tm_prev[second],
                                               reinterpret_cast<T*>(h->hi[h->prv]), h->geo(),
-                                              coef_n<T, NC>(h->ca), tiles_x, n_tiles, h->gw, h->status);
+                                              coef_n<T, NC>(h->ca), tiles_x, n_tiles, h->gw, h->status,
+                                              reinterpret_cast<T*>(h->hi[second]));
     W2D_LAUNCHED("derived-scheme TMA two-step kernel launch");
     return WAVE2D_OK;
 }
@@ -60,10 +63,13 @@ int chain_tma_step(wave2d* h) {
         constexpr int NC = decltype(NCc)::value;
         dispatch_bool(h->bc == WAVE2D_BC_PERIODIC, [&](auto Pc) {
             constexpr bool P = decltype(Pc)::value;
-            dispatch_bool(h->diff_sums, [&](auto Dc) {
-                constexpr bool D = decltype(Dc)::value;
-                rc = (h->dtype == DT_F32) ? launch_tma<float, NC, P, D>(h) : launch_tma<double, NC, P, D>(h);
-            });
+            if (h->dtype == DT_F32) {
+                if (h->diff_form) rc = launch_tma<float, NC, P, true, true>(h);
+                else if (h->diff_sums) rc = launch_tma<float, NC, P, true, false>(h);
+                else rc = launch_tma<float, NC, P, false, false>(h);
+            } else {
+                rc = h->diff_sums ? launch_tma<double, NC, P, true, false>(h) : launch_tma<double, NC, P, false, false>(h);
+            }
         });
     });
     return rc;

@@ -20,7 +20,8 @@
 
 namespace w2d {
 
-template <int DT, int NC, bool PER, bool TRACK>
+// DFORM: L0 receives d^1 = u^1 - u^0 (formed in FP64) instead of u^0.
+template <int DT, int NC, bool PER, bool TRACK, bool DFORM>
 __global__ void __launch_bounds__(256) kc1_first_step(const double* __restrict__ u0,
                                                       const double* __restrict__ v0, Level L0,
                                                       Level L1, Geo g, CoefN<double, NC> ahalf,
@@ -36,11 +37,11 @@ __global__ void __launch_bounds__(256) kc1_first_step(const double* __restrict__
         const double uc = u(0, 0), vc = v(0, 0);
         const double u1 = first_step_chain<NC>(u, v, uc, vc, ahalf, b, tau);
         const size_t o = off(g, i, j);
-        const typename T::V q0 = T::from_d(uc), q1 = T::from_d(u1);
+        const typename T::V q0 = T::from_d(DFORM ? __dsub_rn(u1, uc) : uc), q1 = T::from_d(u1);
         T::st(L0, o, q0);
         T::st(L1, o, q1);
         if (PER) {
-            write_images<DT>(L0, g, i, j, q0, gw);
+            if (!DFORM) write_images<DT>(L0, g, i, j, q0, gw);  // d is read at its own node only
             write_images<DT>(L1, g, i, j, q1, gw);
         }
         if (TRACK) error_terms(T::to_d(q1), exact_at(ex, i, j), s0, s1, m0, m1, rd.status);
@@ -48,10 +49,11 @@ __global__ void __launch_bounds__(256) kc1_first_step(const double* __restrict__
     if (TRACK) reduce_finalize<256>(s0, s1, m0, m1, rd);
 }
 
-template <int DT, int NC, bool PER, bool TRACK, bool DIFF>
+// DFORM: `nxt` receives u^{k+1}; `dpl` holds d^k and receives d^{k+1} in place.
+template <int DT, int NC, bool PER, bool TRACK, bool DIFF, bool DFORM>
 __global__ void __launch_bounds__(256) kc2_simple(Level cur, Level nxt, Geo g,
                                                   CoefN<typename St<DT>::V, NC> a, ExactTab ex,
-                                                  Reduce rd, int gw) {
+                                                  Reduce rd, int gw, Level dpl) {
     using T = St<DT>;
     using V = typename T::V;
     const int i = blockIdx.x * 32 + threadIdx.x;
@@ -61,7 +63,14 @@ __global__ void __launch_bounds__(256) kc2_simple(Level cur, Level nxt, Geo g,
         const size_t o = off(g, i, j);
         const long long P = g.pitch;
         const auto u = [&](int dx, int dy) { return T::ldg(cur, (size_t)((long long)o + dy * P + dx)); };
-        const V r = two_step_chain<NC, DIFF>(u, u(0, 0), T::ld(nxt, o), a);
+        V r;
+        if constexpr (DFORM) {
+            V dn;
+            two_step_chain_dform<NC, DIFF>(u, u(0, 0), T::ld(dpl, o), a, r, dn);
+            T::st(dpl, o, dn);
+        } else {
+            r = two_step_chain<NC, DIFF>(u, u(0, 0), T::ld(nxt, o), a);
+        }
         T::st(nxt, o, r);
         if (PER) write_images<DT>(nxt, g, i, j, r, gw);
         if (TRACK) error_terms(T::to_d(r), exact_at(ex, i, j), s0, s1, m0, m1, rd.status);
@@ -127,10 +136,13 @@ __device__ __forceinline__ ChainRow<T, VEC, H> chain_load_row(const T* row, int 
     return r;
 }
 
-template <typename T, int NC, bool PER, int TH, int NW, int NSTAGES, int MINB, bool DIFF>
+// DFORM: tm_prev stages d^k; u^{k+1} goes to `nxt`, d^{k+1} to `dout` (in
+// place over d^k, which this tile has already staged).
+template <typename T, int NC, bool PER, int TH, int NW, int NSTAGES, int MINB, bool DIFF, bool DFORM>
 __global__ void __launch_bounds__(NW * 32, MINB)
     kc2_tma(const __grid_constant__ CUtensorMap tm_cur, const __grid_constant__ CUtensorMap tm_prev,
-            T* __restrict__ nxt, Geo g, CoefN<T, NC> a, int tiles_x, int n_tiles, int gw, int* status) {
+            T* __restrict__ nxt, Geo g, CoefN<T, NC> a, int tiles_x, int n_tiles, int gw, int* status,
+            T* __restrict__ dout) {
     using C = ChainTmaCfg<T, NC, TH, NW>;
     constexpr int VEC = C::VEC, R = C::R, H = C::H, HB = C::HB, TW = C::TW, BOX_W = C::BOX_W,
                   RPW = C::RPW;
@@ -201,15 +213,29 @@ __global__ void __launch_bounds__(NW * 32, MINB)
                 const double2 p = *reinterpret_cast<const double2*>(prev_s + (r0 + r) * TW + lane * 2);
                 pv[0] = p.x; pv[1] = p.y;
             }
-            T out[VEC];
+            T out[VEC], dnew[VEC];
 #pragma unroll
             for (int e = 0; e < VEC; ++e) {
                 const auto u = [&](int dx, int dy) -> T { return win[R + dy].a[H + e + dx]; };
-                out[e] = two_step_chain<NC, DIFF>(u, u(0, 0), pv[e], a);
+                if constexpr (DFORM) two_step_chain_dform<NC, DIFF>(u, u(0, 0), pv[e], a, out[e], dnew[e]);
+                else out[e] = two_step_chain<NC, DIFF>(u, u(0, 0), pv[e], a);
             }
             const int y = ty * TH + r0 + r;
             if (y < g.ny) {
                 T* gp = nxt + off(g, x, y);
+                if constexpr (DFORM) {
+                    T* dp = dout + off(g, x, y);
+                    if (x + VEC <= g.nx) {
+                        if constexpr (VEC == 4)
+                            *reinterpret_cast<float4*>(dp) = make_float4(dnew[0], dnew[1], dnew[2], dnew[3]);
+                        else
+                            *reinterpret_cast<double2*>(dp) = make_double2(dnew[0], dnew[1]);
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < VEC; ++e)
+                            if (x + e < g.nx) dp[e] = dnew[e];
+                    }
+                }
                 if (x + VEC <= g.nx) {
                     if constexpr (VEC == 4) {
                         const float4 v = make_float4(out[0], out[1], out[2], out[3]);

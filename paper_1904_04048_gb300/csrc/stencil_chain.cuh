@@ -108,6 +108,19 @@ __device__ __forceinline__ V two_step_chain(const F& u, V c, V prev, const CoefN
     return vadd(base, L);
 }
 
+// Difference form of the two-step (the same recursion, Eq. A2, on the pair
+// u^k, d^k = u^k - u^{k-1}):  d^{k+1} = d^k + Lambda_a(u^k),
+// u^{k+1} = u^k + d^{k+1}.  The small increment Lambda is added to the small
+// d, and the rounding of u^{k+1} enters u once instead of being integrated
+// twice by the recursion.
+template <int NC, bool DIFF, typename V, typename F>
+__device__ __forceinline__ void two_step_chain_dform(const F& u, V c, V d, const CoefN<V, NC>& a, V& u_next,
+                                                     V& d_next) {
+    const V L = lambda_chain<NC, DIFF>(u, c, a);
+    d_next = vadd(d, L);
+    u_next = vadd(c, d_next);
+}
+
 // First step (Eq. A1), FP64.
 template <int NC, typename FU, typename FV>
 __device__ __forceinline__ double first_step_chain(const FU& u, const FV& v, double uc, double vc,

@@ -601,6 +601,13 @@ static int check_status(wave2d* h) {
     return WAVE2D_OK;
 }
 
+// out = a - b (FP64), for the conversions between (u^{k-1}, u^k) and the
+// difference form's (d^k, u^k).
+__global__ void k_combine(const double* a, const double* b, double* out, size_t n) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = __dsub_rn(a[i], b[i]);
+}
+
 // Self-test of the bounded wait: an mbarrier that nothing ever completes is
 // waited on with a short limit; the wait gives up, raises STATUS_TIMEOUT and
 // the kernel returns.  No copy is in flight, so nothing needs draining.
@@ -661,6 +668,8 @@ static int check_grid(const wave2d_grid* grid, double hh, double tau, double c, 
     if (grid->flags & ~allowed_flags) return set_error(WAVE2D_ERR_ARG, "unsupported flags 0x%x", grid->flags);
     if ((grid->flags & WAVE2D_DIFF_SUMS) && grid->dtype == WAVE2D_F32X2)
         return set_error(WAVE2D_ERR_ARG, "difference sums are available for F32 and F64 storage");
+    if ((grid->flags & WAVE2D_DIFF_FORM) && grid->dtype != WAVE2D_F32)
+        return set_error(WAVE2D_ERR_ARG, "the difference form is available for F32 storage");
     if (!(hh > 0) || !(tau > 0) || !(c > 0) || !std::isfinite(hh) || !std::isfinite(tau) || !std::isfinite(c))
         return set_error(WAVE2D_ERR_ARG, "h, tau and c must be positive and finite");
     return WAVE2D_OK;
@@ -685,7 +694,7 @@ static int create_device_state(wave2d* h, const wave2d_grid* grid) {
     // (the temporal kernel writes out of place); FP32x2 keeps hi and lo
     // planes of two levels; FP64 two levels.
     h->elem = (h->dtype == WAVE2D_F64) ? 8 : 4;
-    h->nlevels = (h->dtype == WAVE2D_F32 && h->nclass == 0) ? 4 : 2;
+    h->nlevels = (h->dtype == WAVE2D_F32 && h->nclass == 0) ? 4 : h->diff_form ? 3 : 2;
     h->gw = h->R;
     h->G = kGhost;
     h->pitch = (int)round_up((size_t)h->nx + 2 * kGhost, 32);
@@ -742,7 +751,8 @@ int wave2d_create(const wave2d_grid* grid, double hh, double tau, double c, int 
     *out = nullptr;
     if (scheme != 5 && scheme != 9 && scheme != 13)
         return set_error(WAVE2D_ERR_ARG, "scheme must be 5, 9 or 13 (got %d)", scheme);
-    int rc = check_grid(grid, hh, tau, c, WAVE2D_ALLOW_UNSTABLE | WAVE2D_CONVENTIONAL | WAVE2D_DIFF_SUMS);
+    int rc = check_grid(grid, hh, tau, c,
+                        WAVE2D_ALLOW_UNSTABLE | WAVE2D_CONVENTIONAL | WAVE2D_DIFF_SUMS | WAVE2D_DIFF_FORM);
     if (rc != WAVE2D_OK) return rc;
     const bool conventional = (grid->flags & WAVE2D_CONVENTIONAL) != 0;
     const double lam = c * tau / hh;
@@ -759,10 +769,11 @@ int wave2d_create(const wave2d_grid* grid, double hh, double tau, double c, int 
     h->npoints = scheme;
     h->lam_max = lmax;
     scheme_coefficients(scheme, conventional, lam, h->a, h->b);
-    if (grid->flags & WAVE2D_DIFF_SUMS) {
-        // The class-chain kernels carry the difference sums: the Section 6
-        // scheme is its first one, two or three classes.
+    if (grid->flags & (WAVE2D_DIFF_SUMS | WAVE2D_DIFF_FORM)) {
+        // The class-chain kernels carry the difference sums and form: the
+        // Section 6 scheme is its first one, two or three classes.
         h->diff_sums = true;
+        h->diff_form = (grid->flags & WAVE2D_DIFF_FORM) != 0;
         h->nclass = scheme == 5 ? 1 : scheme == 9 ? 2 : 3;
         for (int q = 0; q < 3; ++q) {
             h->ca[q] = h->a[q];
@@ -785,7 +796,7 @@ int wave2d_create_scheme(const wave2d_grid* grid, double hh, double tau, double 
     *out = nullptr;
     int rc = check_scheme(s);
     if (rc != WAVE2D_OK) return rc;
-    rc = check_grid(grid, hh, tau, c, WAVE2D_ALLOW_UNSTABLE | WAVE2D_DIFF_SUMS);
+    rc = check_grid(grid, hh, tau, c, WAVE2D_ALLOW_UNSTABLE | WAVE2D_DIFF_SUMS | WAVE2D_DIFF_FORM);
     if (rc != WAVE2D_OK) return rc;
     const double lam = c * tau / hh;
     const double lmax = scheme_lambda_max(s);
@@ -796,7 +807,8 @@ int wave2d_create_scheme(const wave2d_grid* grid, double hh, double tau, double 
     if (!h) return set_error(WAVE2D_ERR_OOM, "host allocation failed");
     set_problem(h, grid, hh, tau, c);
     h->scheme = 0;
-    h->diff_sums = (grid->flags & WAVE2D_DIFF_SUMS) != 0;
+    h->diff_form = (grid->flags & WAVE2D_DIFF_FORM) != 0;
+    h->diff_sums = (grid->flags & (WAVE2D_DIFF_SUMS | WAVE2D_DIFF_FORM)) != 0;
     h->nclass = s->n_classes;
     h->R = chain_radius(s->n_classes);
     h->npoints = chain_points(s->n_classes);
@@ -998,8 +1010,10 @@ int wave2d_get_state(wave2d_t h, double* u_prev, double* u_cur, int64_t* k) {
     if (!stage) return set_error(WAVE2D_ERR_OOM, "staging allocation failed");
     dispatch_dt(h->dtype, [&](auto DTc) {
         constexpr int DT = decltype(DTc)::value;
-        k_pack<DT><<<grid2d(h), dim3(32, 8), 0, h->stream>>>(h->level(h->prv), h->geo(), stage);
+        k_pack<DT><<<grid2d(h), dim3(32, 8), 0, h->stream>>>(h->level(h->diff_form ? 2 : h->prv), h->geo(), stage);
         k_pack<DT><<<grid2d(h), dim3(32, 8), 0, h->stream>>>(h->level(h->cur), h->geo(), stage + n);
+        if (h->diff_form)  // u^{k-1} = u^k - d^k, in FP64
+            k_combine<<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(stage + n, stage, stage, n);
     });
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess && u_prev)
@@ -1009,7 +1023,7 @@ int wave2d_get_state(wave2d_t h, double* u_prev, double* u_cur, int64_t* k) {
     dev_free(h->alloc, stage, 2 * n * sizeof(double), h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_fail(e, "get_state");
-    g_launches.fetch_add(2);
+    g_launches.fetch_add(h->diff_form ? 3 : 2);
     if (k) *k = h->k;
     return check_status(h);
 }
@@ -1032,17 +1046,29 @@ int wave2d_set_state(wave2d_t h, const double* u_prev, const double* u_cur, int6
     }
     h->cur = 0;
     h->prv = 1;
+    double* dstage = nullptr;
+    if (h->diff_form) {  // d^k = u^k - u^{k-1}, formed in FP64
+        dstage = (double*)dev_alloc(h->alloc, n * sizeof(double), h->stream);
+        if (!dstage) {
+            if (stage) dev_free(h->alloc, stage, 2 * n * sizeof(double), h->stream);
+            return set_error(WAVE2D_ERR_OOM, "staging allocation failed");
+        }
+        k_combine<<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(dc, dp, dstage, n);
+        dp = dstage;
+    }
     dispatch_dt(h->dtype, [&](auto DTc) {
         constexpr int DT = decltype(DTc)::value;
         dispatch_bool(h->bc == WAVE2D_BC_PERIODIC, [&](auto Pc) {
-            k_unpack<DT, decltype(Pc)::value><<<grid2d(h), dim3(32, 8), 0, h->stream>>>(dp, h->level(1), h->geo(), h->gw);
+            k_unpack<DT, decltype(Pc)::value><<<grid2d(h), dim3(32, 8), 0, h->stream>>>(
+                dp, h->level(h->diff_form ? 2 : 1), h->geo(), h->gw);
             k_unpack<DT, decltype(Pc)::value><<<grid2d(h), dim3(32, 8), 0, h->stream>>>(dc, h->level(0), h->geo(), h->gw);
         });
     });
     cudaError_t e = cudaGetLastError();
     if (stage) dev_free(h->alloc, stage, 2 * n * sizeof(double), h->stream);
+    if (dstage) dev_free(h->alloc, dstage, n * sizeof(double), h->stream);
     if (e != cudaSuccess) return cuda_fail(e, "set_state");
-    g_launches.fetch_add(2);
+    g_launches.fetch_add(h->diff_form ? 3 : 2);
     h->k = k;
     h->initialized = true;
     drop_graphs(h);
@@ -1055,13 +1081,13 @@ int64_t wave2d_raw_bytes(wave2d_t h) {
 }
 
 // Raw layout: [u^{k-1} hi][u^k hi] (+ [u^{k-1} lo][u^k lo] for F32X2), each
-// plane_bytes long, ghost ring included.
+// plane_bytes long, ghost ring included; difference form: [d^k][u^k].
 int wave2d_get_raw(wave2d_t h, void* dst, int64_t bytes, int64_t* k) {
     if (!h || !dst) return set_error(WAVE2D_ERR_ARG, "null argument");
     if (!h->initialized) return set_error(WAVE2D_ERR_STATE, "no state yet");
     if (bytes < wave2d_raw_bytes(h)) return set_error(WAVE2D_ERR_ARG, "buffer too small");
     char* d = (char*)dst;
-    const int order[2] = {h->prv, h->cur};
+    const int order[2] = {h->diff_form ? 2 : h->prv, h->cur};
     for (int q = 0; q < 2; ++q) {
         W2D_CUDA(cudaMemcpyAsync(d + q * h->plane_bytes, h->hi[order[q]], h->plane_bytes, cudaMemcpyDeviceToHost,
                                  h->stream),
@@ -1081,10 +1107,12 @@ int wave2d_set_raw(wave2d_t h, const void* src, int64_t bytes, int64_t k) {
     if (k < 1) return set_error(WAVE2D_ERR_ARG, "level index k must be >= 1");
     if (bytes < wave2d_raw_bytes(h)) return set_error(WAVE2D_ERR_ARG, "buffer too small");
     const char* s = (const char*)src;
-    h->cur = 1;  // plane 0 <- u^{k-1}, plane 1 <- u^k
+    h->cur = 1;  // plane 0 <- u^{k-1}, plane 1 <- u^k (difference form: plane 2 <- d^k)
     h->prv = 0;
     for (int q = 0; q < 2; ++q) {
-        W2D_CUDA(cudaMemcpyAsync(h->hi[q], s + q * h->plane_bytes, h->plane_bytes, cudaMemcpyHostToDevice, h->stream),
+        const int plane = (q == 0 && h->diff_form) ? 2 : q;
+        W2D_CUDA(cudaMemcpyAsync(h->hi[plane], s + q * h->plane_bytes, h->plane_bytes, cudaMemcpyHostToDevice,
+                                 h->stream),
                  "raw copy");
         if (h->lo[0])
             W2D_CUDA(cudaMemcpyAsync(h->lo[q], s + (2 + q) * h->plane_bytes, h->plane_bytes, cudaMemcpyHostToDevice,
@@ -1143,7 +1171,7 @@ int wave2d_autotune(wave2d_t h, int64_t steps, wave2d_tune* best) {
     const int cur0 = h->cur, prv0 = h->prv;
     const int64_t k0 = h->k;
     auto copy_levels = [&](bool save) -> int {
-        const int planes[2] = {cur0, prv0};
+        const int planes[2] = {cur0, h->diff_form ? 2 : prv0};
         for (int q = 0; q < 2; ++q)
             for (int part = 0; part < np; ++part) {
                 void* dev = part == 0 ? h->hi[planes[q]] : h->lo[planes[q]];

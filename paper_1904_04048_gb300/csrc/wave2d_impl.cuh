@@ -67,6 +67,7 @@ struct wave2d {
     int nclass = 0, npoints = 0;
     double ca[8] = {}, cb[8] = {};
     bool diff_sums = false;  // WAVE2D_DIFF_SUMS: class sums from differences to the centre
+    bool diff_form = false;  // WAVE2D_DIFF_FORM: planes u^k (cur), scratch (prv), d^k (plane 2)
     // device
     int device = 0, num_sms = 0, l2_bytes = 0;
     cudaStream_t stream = nullptr;
