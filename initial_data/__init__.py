@@ -20,11 +20,12 @@ import numpy as np
 
 BC_ZERO = 0
 BC_PERIODIC = 1
+BC_ODD = 2  # the zero-boundary node set with odd continuation beyond the boundary nodes
 
 
 def x_offset(bc: int) -> float:
     """Offset (in units of h) of node 0 from the origin."""
-    return 1.0 if bc == BC_ZERO else 0.0
+    return 0.0 if bc == BC_PERIODIC else 1.0
 
 
 def coords(n: int, h: float, bc: int) -> np.ndarray:

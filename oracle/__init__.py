@@ -39,6 +39,7 @@ _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
 
 BC_ZERO = 0
 BC_PERIODIC = 1
+BC_ODD = 2
 EXACT_NONE = 0
 EXACT_STANDING = 1
 EXACT_PLANE = 2

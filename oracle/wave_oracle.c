@@ -21,6 +21,13 @@
  *                    (the grid boundary condition of Section 6.1.2, extended
  *                    to a zero ring of width 2 for the 13-point scheme);
  *   ORC_BC_PERIODIC  indices wrap modulo nx / ny (Section 6.3).
+ *   ORC_BC_ODD       the Dirichlet condition of Section 6.1.2 (u = 0 on the
+ *                    boundary nodes i = -1 and i = nx, likewise in j) with the
+ *                    field continued beyond them as an odd function:
+ *                    u(-1 - k) = -u(-1 + k), u(nx + k) = -u(nx - k).  For
+ *                    radius-1 stencils this reads only the boundary nodes and
+ *                    equals ORC_BC_ZERO; for wider ones it is the reflection
+ *                    the paper leaves open for the 13-point scheme.
  */
 #include <math.h>
 #include <stdint.h>
@@ -31,7 +38,20 @@
 #include <omp.h>
 #endif
 
-enum { ORC_BC_ZERO = 0, ORC_BC_PERIODIC = 1 };
+enum { ORC_BC_ZERO = 0, ORC_BC_PERIODIC = 1, ORC_BC_ODD = 2 };
+
+/* Odd continuation of an index about the boundary nodes -1 and n: returns the
+ * interior index and multiplies *sign by -1 per reflection; -1 for a
+ * boundary node (value 0). */
+static int odd_index(int i, int n, double *sign)
+{
+    for (;;) {
+        if (i == -1 || i == n) return -1;
+        if (i < -1) { i = -2 - i; *sign = -*sign; continue; }
+        if (i > n) { i = 2 * n - i; *sign = -*sign; continue; }
+        return i;
+    }
+}
 enum { ORC_EXACT_NONE = 0, ORC_EXACT_STANDING = 1, ORC_EXACT_PLANE = 2 };
 
 /* Value of a grid function at node (i, j) under the boundary rule. */
@@ -41,6 +61,13 @@ static double at(const double *u, int nx, int ny, int bc, int i, int j)
         i = ((i % nx) + nx) % nx;
         j = ((j % ny) + ny) % ny;
         return u[(size_t)j * nx + i];
+    }
+    if (bc == ORC_BC_ODD) {
+        double sign = 1.0;
+        i = odd_index(i, nx, &sign);
+        j = odd_index(j, ny, &sign);
+        if (i < 0 || j < 0) return 0.0;
+        return sign * u[(size_t)j * nx + i];
     }
     if (i < 0 || i >= nx || j < 0 || j >= ny)
         return 0.0;
