@@ -36,6 +36,14 @@
  *                      (the grid boundary condition u = 0 of Section 6.1.2,
  *                      a zero ring of width 2 for scheme 13);
  *   WAVE2D_BC_PERIODIC indices wrap modulo nx and ny (Section 6.3).
+ *   WAVE2D_BC_ODD      the zero boundary's node set and boundary nodes
+ *                      (u = 0 at i = -1, i = nx and likewise in j), with the
+ *                      field continued beyond them as an odd function,
+ *                      u(-1 - k) = -u(-1 + k), u(nx + k) = -u(nx - k): for
+ *                      radius-1 stencils the same as WAVE2D_BC_ZERO, for the
+ *                      13-point and derived schemes a Dirichlet condition the
+ *                      paper leaves open (it is exact for sine modes).  One-
+ *                      node and TMA kernels (no temporal blocking, no batches).
  *   Errors: every int function returns WAVE2D_OK (0) or a negative status;
  *   wave2d_last_error() then gives a message (thread-local).  Kernels run
  *   asynchronously on the handle's stream; a device-side failure surfaces as
@@ -66,7 +74,7 @@ enum {
     WAVE2D_ERR_STATE = -7      /* call out of order (e.g. stepping before init) */
 };
 
-enum { WAVE2D_BC_ZERO = 0, WAVE2D_BC_PERIODIC = 1 };
+enum { WAVE2D_BC_ZERO = 0, WAVE2D_BC_PERIODIC = 1, WAVE2D_BC_ODD = 2 };
 
 /* Storage / arithmetic type of the time levels.  The first step always
  * computes in FP64 and rounds into the storage type; norms reduce in FP64.

@@ -22,7 +22,8 @@ OBJ = os.path.join(PKG, "_objs")
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
               "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off", "-I" + os.path.join(ROOT, "include")]
 
-SOURCES = ["wave2d.cu", "chain.cu", "chain_tma.cu", "scheme.cu", "noalloc.cu", "batch.cu", "server.cu"]
+SOURCES = ["wave2d.cu", "chain.cu", "chain_f32.cu", "chain_f64.cu", "chain_f32x2.cu", "chain_tma.cu", "scheme.cu",
+           "noalloc.cu", "batch.cu", "server.cu"]
 
 
 def _nvcc():

@@ -466,6 +466,8 @@ int wave2d_batch_create(wave2d_t* handles, int n, const wave2d_tune* opt, wave2d
     for (int i = 0; i < n; ++i) {
         if (!handles[i]) return set_error(WAVE2D_ERR_ARG, "null handle %d", i);
         if (handles[i]->dtype != WAVE2D_F32) return set_error(WAVE2D_ERR_ARG, "batched stepping needs F32 storage");
+        if (handles[i]->bc == WAVE2D_BC_ODD)
+            return set_error(WAVE2D_ERR_ARG, "batched stepping covers the zero and periodic boundaries");
         if (handles[i]->nclass > 0)
             return set_error(WAVE2D_ERR_ARG,
                              "batched stepping covers the 5-, 9- and 13-point schemes with plain sums only");
@@ -617,7 +619,7 @@ static int batch_run_impl(wave2d_batch_t b, const int64_t* steps) {
                 const long long total = (long long)(h->nx + 2 * h->gw) * (h->ny + 2 * h->gw);
                 const int grid = (int)std::min<long long>((total + 255) / 256, 8LL * h->num_sms);
                 for (int p : {h->cur, h->prv}) {
-                    k_refresh_ghosts<DT_F32><<<grid, 256, 0, b->stream>>>(h->level(p), h->geo(), h->gw);
+                    k_refresh_ghosts<DT_F32, BCM_PERIODIC><<<grid, 256, 0, b->stream>>>(h->level(p), h->geo(), h->gw);
                     cudaError_t e = cudaGetLastError();
                     if (e != cudaSuccess) return cuda_fail(e, "ghost refresh");
                     g_launches.fetch_add(1);

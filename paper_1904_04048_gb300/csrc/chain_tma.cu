@@ -20,12 +20,12 @@ struct ChainTile {
     static constexpr int MINB = (!F32 && NC >= 8) ? 1 : 2;
 };
 
-template <typename T, int NC, bool PER, bool DIFF, bool DFORM>
+template <typename T, int NC, int BCM, bool DIFF, bool DFORM>
 int launch_tma(wave2d* h) {
     using Tile = ChainTile<T, NC>;
     constexpr int kNW = Tile::NW, kTH = Tile::TH;
     using C = ChainTmaCfg<T, NC, kTH, kNW>;
-    auto kern = kc2_tma<T, NC, PER, kTH, kNW, Tile::STAGES, Tile::MINB, DIFF, DFORM>;
+    auto kern = kc2_tma<T, NC, BCM, kTH, kNW, Tile::STAGES, Tile::MINB, DIFF, DFORM>;
     const int smem = 2048 + Tile::STAGES * C::STAGE_BYTES;
     static thread_local int configured_smem = -1;  // per instantiation
     if (configured_smem != smem) {
@@ -61,8 +61,8 @@ int chain_tma_step(wave2d* h) {
     int rc = WAVE2D_OK;
     dispatch_nc(h->nclass, [&](auto NCc) {
         constexpr int NC = decltype(NCc)::value;
-        dispatch_bool(h->bc == WAVE2D_BC_PERIODIC, [&](auto Pc) {
-            constexpr bool P = decltype(Pc)::value;
+        dispatch_bcm(h->bc, [&](auto Pc) {
+            constexpr int P = decltype(Pc)::value;
             if (h->dtype == DT_F32) {
                 if (h->diff_form) rc = launch_tma<float, NC, P, true, true>(h);
                 else if (h->diff_sums) rc = launch_tma<float, NC, P, true, false>(h);

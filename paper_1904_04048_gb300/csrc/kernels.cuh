@@ -15,6 +15,10 @@
 // writes a node within gw of an edge also writes its periodic images into the
 // first gw rings (gw = R, the stencil radius, for one-level kernels; deeper
 // when temporal blocking reads a wider halo), so readers never wrap indices.
+// Odd boundary (the zero boundary continued as an odd function beyond the
+// boundary nodes -1 and nx): writers store the negated mirror images
+// u(-2 - i) = -u(i), u(2 nx - i) = -u(i) (and their products at the corners)
+// in the first gw rings; the boundary nodes themselves stay zero.
 #pragma once
 #include <cuda.h>
 #include <cuda_runtime.h>
@@ -26,6 +30,7 @@
 namespace w2d {
 
 enum { DT_F64 = 0, DT_F32 = 1, DT_F32X2 = 2 };
+enum { BCM_ZERO = 0, BCM_PERIODIC = 1, BCM_ODD = 2 };  // boundary modes (WAVE2D_BC_*)
 enum { STATUS_NONFINITE = 1, STATUS_TIMEOUT = 2 };
 
 struct Level {
@@ -127,6 +132,42 @@ __device__ __forceinline__ void store_vec_images(VT* base, const Geo& g, int x, 
         if (ylo) *at(x - g.nx, y + g.ny) = v;
         if (yhi) *at(x - g.nx, y - g.ny) = v;
     }
+}
+
+__device__ __forceinline__ float vneg(float a) { return -a; }
+__device__ __forceinline__ double vneg(double a) { return -a; }
+__device__ __forceinline__ df vneg(df a) { return df_neg(a); }
+
+// Odd continuation: the positions p of the ghost band [-gw, n + gw) that hold
+// node i (sign +1: p = i + m P) or its negation (sign -1: p = -2 - i + m P),
+// P = 2 (n + 1) the period of the odd extension; the boundary nodes -1 and n
+// are never among them.
+template <int DT>
+__device__ __forceinline__ void write_images_odd(const Level& L, const Geo& g, int i, int j,
+                                                 typename St<DT>::V v, int gw) {
+    if (i >= gw && i < g.nx - gw && j >= gw && j < g.ny - gw) return;
+    const int Px = 2 * (g.nx + 1), Py = 2 * (g.ny + 1);
+    const int mx = (gw + Px - 1) / Px + 1, my = (gw + Py - 1) / Py + 1;
+    const typename St<DT>::V nv = vneg(v);
+    for (int ky = -my; ky <= my; ++ky)
+        for (int ty = 0; ty < 2; ++ty) {
+            const int jj = ty ? (-2 - j + ky * Py) : (j + ky * Py);
+            if (jj < -gw || jj >= g.ny + gw || jj == -1 || jj == g.ny) continue;
+            for (int kx = -mx; kx <= mx; ++kx)
+                for (int tx = 0; tx < 2; ++tx) {
+                    const int ii = tx ? (-2 - i + kx * Px) : (i + kx * Px);
+                    if (ii < -gw || ii >= g.nx + gw || ii == -1 || ii == g.nx) continue;
+                    if (ii >= 0 && ii < g.nx && jj >= 0 && jj < g.ny) continue;  // the node itself
+                    St<DT>::st(L, off(g, ii, jj), (tx ^ ty) ? nv : v);
+                }
+        }
+}
+
+template <int DT, int BCM>
+__device__ __forceinline__ void write_images_bc(const Level& L, const Geo& g, int i, int j,
+                                                typename St<DT>::V v, int gw) {
+    if constexpr (BCM == BCM_PERIODIC) write_images<DT>(L, g, i, j, v, gw);
+    else if constexpr (BCM == BCM_ODD) write_images_odd<DT>(L, g, i, j, v, gw);
 }
 
 // ---------------------------------------------------------------------------
@@ -266,11 +307,28 @@ __device__ __forceinline__ void error_terms(double v, double ue, double& s0, dou
 // ---------------------------------------------------------------------------
 // K1: first time step (Eq. A1), FP64, one node per thread.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ double fetch_bc(const double* __restrict__ a, int nx, int ny, bool periodic,
-                                           int i, int j) {
-    if (periodic) {
+// Interior index of position i under the odd continuation about the
+// boundary nodes -1 and n (sign flipped per reflection); -1 for a boundary
+// node.
+__device__ __forceinline__ int odd_index(int i, int n, double& sign) {
+    for (;;) {
+        if (i == -1 || i == n) return -1;
+        if (i < -1) { i = -2 - i; sign = -sign; continue; }
+        if (i > n) { i = 2 * n - i; sign = -sign; continue; }
+        return i;
+    }
+}
+
+__device__ __forceinline__ double fetch_bc(const double* __restrict__ a, int nx, int ny, int bcm, int i, int j) {
+    if (bcm == BCM_PERIODIC) {
         i = ((i % nx) + nx) % nx;
         j = ((j % ny) + ny) % ny;
+    } else if (bcm == BCM_ODD) {
+        double sign = 1.0;
+        i = odd_index(i, nx, sign);
+        j = odd_index(j, ny, sign);
+        if (i < 0 || j < 0) return 0.0;
+        return sign * __ldg(a + (size_t)j * nx + i);
     } else if (i < 0 || i >= nx || j < 0 || j >= ny) {
         return 0.0;
     }
@@ -278,7 +336,7 @@ __device__ __forceinline__ double fetch_bc(const double* __restrict__ a, int nx,
 }
 
 __device__ __forceinline__ Nbr<double> gather_bc(const double* __restrict__ a, int nx, int ny,
-                                                 bool per, int i, int j) {
+                                                 int per, int i, int j) {
     Nbr<double> u;
     u.c = fetch_bc(a, nx, ny, per, i, j);
     u.e = fetch_bc(a, nx, ny, per, i + 1, j);
@@ -296,7 +354,7 @@ __device__ __forceinline__ Nbr<double> gather_bc(const double* __restrict__ a, i
     return u;
 }
 
-template <int DT, int S, bool PER, bool TRACK>
+template <int DT, int S, int BCM, bool TRACK>
 __global__ void __launch_bounds__(256) k1_first_step(const double* __restrict__ u0,
                                                      const double* __restrict__ v0, Level L0,
                                                      Level L1, Geo g, Coef3<double> ahalf,
@@ -307,16 +365,16 @@ __global__ void __launch_bounds__(256) k1_first_step(const double* __restrict__ 
     const int j = blockIdx.y * 8 + threadIdx.y;
     double s0 = 0, s1 = 0, m0 = 0, m1 = 0;
     if (i < g.nx && j < g.ny) {
-        const Nbr<double> u = gather_bc(u0, g.nx, g.ny, PER, i, j);
-        const Nbr<double> v = gather_bc(v0, g.nx, g.ny, PER, i, j);
+        const Nbr<double> u = gather_bc(u0, g.nx, g.ny, BCM, i, j);
+        const Nbr<double> v = gather_bc(v0, g.nx, g.ny, BCM, i, j);
         const double u1 = first_step_update<S>(u, v, ahalf, b, tau);
         const size_t o = off(g, i, j);
         const typename T::V q0 = T::from_d(u.c), q1 = T::from_d(u1);
         T::st(L0, o, q0);
         T::st(L1, o, q1);
-        if (PER) {
-            write_images<DT>(L0, g, i, j, q0, gw);
-            write_images<DT>(L1, g, i, j, q1, gw);
+        if (BCM != BCM_ZERO) {
+            write_images_bc<DT, BCM>(L0, g, i, j, q0, gw);
+            write_images_bc<DT, BCM>(L1, g, i, j, q1, gw);
         }
         if (TRACK) error_terms(T::to_d(q1), exact_at(ex, i, j), s0, s1, m0, m1, rd.status);
     }
@@ -326,7 +384,7 @@ __global__ void __launch_bounds__(256) k1_first_step(const double* __restrict__ 
 // ---------------------------------------------------------------------------
 // K2 simple: one node per thread, neighbours through the read-only cache.
 // ---------------------------------------------------------------------------
-template <int DT, int S, bool PER, bool TRACK>
+template <int DT, int S, int BCM, bool TRACK>
 __global__ void __launch_bounds__(256) k2_simple(Level cur, Level nxt, Geo g,
                                                  Coef3<typename St<DT>::V> a, ExactTab ex,
                                                  Reduce rd, int gw) {
@@ -359,7 +417,7 @@ __global__ void __launch_bounds__(256) k2_simple(Level cur, Level nxt, Geo g,
         const V p = T::ld(nxt, o);
         const V r = two_step_update<S>(u, p, a);
         T::st(nxt, o, r);
-        if (PER) write_images<DT>(nxt, g, i, j, r, gw);
+        if (BCM != BCM_ZERO) write_images_bc<DT, BCM>(nxt, g, i, j, r, gw);
         if (TRACK) error_terms(T::to_d(r), exact_at(ex, i, j), s0, s1, m0, m1, rd.status);
     }
     if (TRACK) reduce_finalize<256>(s0, s1, m0, m1, rd);
@@ -388,13 +446,13 @@ __global__ void __launch_bounds__(256) k_pack(Level L, Geo g, double* __restrict
     if (i < g.nx && j < g.ny) out[(size_t)j * g.nx + i] = St<DT>::to_d(St<DT>::ld(L, off(g, i, j)));
 }
 
-template <int DT, bool PER>
+template <int DT, int BCM>
 __global__ void __launch_bounds__(256) k_unpack(const double* __restrict__ in, Level L, Geo g, int gw) {
     const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y;
     if (i < g.nx && j < g.ny) {
         const typename St<DT>::V v = St<DT>::from_d(in[(size_t)j * g.nx + i]);
         St<DT>::st(L, off(g, i, j), v);
-        if (PER) write_images<DT>(L, g, i, j, v, gw);
+        if (BCM != BCM_ZERO) write_images_bc<DT, BCM>(L, g, i, j, v, gw);
     }
 }
 
@@ -519,7 +577,7 @@ __device__ __forceinline__ RowBuf<T, NV> load_row(const T* row, int lane) {
     return r;
 }
 
-template <typename T, int S, bool PER, int TH, int NW, int NSTAGES>
+template <typename T, int S, int BCM, int TH, int NW, int NSTAGES>
 __global__ void __launch_bounds__(NW * 32, 1)
     k2_tma(const __grid_constant__ CUtensorMap tm_cur, const __grid_constant__ CUtensorMap tm_prev,
            T* __restrict__ nxt, Geo g, Coef3<T> a, int tiles_x, int n_tiles, int gw, int* status) {
@@ -570,9 +628,10 @@ __global__ void __launch_bounds__(NW * 32, 1)
         const int tx = t % tiles_x, ty = t / tiles_x;
         const int x = tx * TW + lane * VEC;  // first column of this lane's vector
         const int r0 = warp * RPW;            // first output row of this warp (tile coords)
-        const bool edge = PER && (tx * TW < gw || tx * TW + TW > g.nx - gw || ty * TH < gw ||
-                                  ty * TH + TH > g.ny - gw);
-        const bool vec_images = (g.nx % VEC == 0) && g.nx >= 2 * gw && g.ny >= 2 * gw;
+        const bool edge = BCM != BCM_ZERO && (tx * TW < gw || tx * TW + TW > g.nx - gw || ty * TH < gw ||
+                                              ty * TH + TH > g.ny - gw);
+        // whole-vector images: periodic mode only (odd images are mirrored)
+        const bool vec_images = BCM == BCM_PERIODIC && (g.nx % VEC == 0) && g.nx >= 2 * gw && g.ny >= 2 * gw;
 
         // register window: win[q] holds tile row (r - R + q) of u^k
         RowBuf<T, VEC> win[2 * R + 1];
@@ -638,8 +697,9 @@ __global__ void __launch_bounds__(NW * 32, 1)
             }
         }
         if (edge && !vec_images) {
-            // Grids too small or not a multiple of the vector width: images
-            // node by node, in a rolled loop that re-reads the stored values.
+            // Odd images, or grids too small or not a multiple of the vector
+            // width: images node by node, in a rolled loop that re-reads the
+            // stored values.
             const Level L{nxt, nullptr};
 #pragma unroll 1
             for (int r = 0; r < RPW; ++r) {
@@ -647,7 +707,7 @@ __global__ void __launch_bounds__(NW * 32, 1)
                 if (y >= g.ny) break;
 #pragma unroll 1
                 for (int e = 0; e < VEC; ++e)
-                    if (x + e < g.nx) write_images<DT>(L, g, x + e, y, nxt[off(g, x + e, y)], gw);
+                    if (x + e < g.nx) write_images_bc<DT, BCM>(L, g, x + e, y, nxt[off(g, x + e, y)], gw);
             }
         }
         __syncthreads();  // every warp is done with stage s

@@ -21,7 +21,7 @@
 namespace w2d {
 
 // DFORM: L0 receives d^1 = u^1 - u^0 (formed in FP64) instead of u^0.
-template <int DT, int NC, bool PER, bool TRACK, bool DFORM>
+template <int DT, int NC, int BCM, bool TRACK, bool DFORM>
 __global__ void __launch_bounds__(256) kc1_first_step(const double* __restrict__ u0,
                                                       const double* __restrict__ v0, Level L0,
                                                       Level L1, Geo g, CoefN<double, NC> ahalf,
@@ -32,17 +32,17 @@ __global__ void __launch_bounds__(256) kc1_first_step(const double* __restrict__
     const int j = blockIdx.y * 8 + threadIdx.y;
     double s0 = 0, s1 = 0, m0 = 0, m1 = 0;
     if (i < g.nx && j < g.ny) {
-        const auto u = [&](int dx, int dy) { return fetch_bc(u0, g.nx, g.ny, PER, i + dx, j + dy); };
-        const auto v = [&](int dx, int dy) { return fetch_bc(v0, g.nx, g.ny, PER, i + dx, j + dy); };
+        const auto u = [&](int dx, int dy) { return fetch_bc(u0, g.nx, g.ny, BCM, i + dx, j + dy); };
+        const auto v = [&](int dx, int dy) { return fetch_bc(v0, g.nx, g.ny, BCM, i + dx, j + dy); };
         const double uc = u(0, 0), vc = v(0, 0);
         const double u1 = first_step_chain<NC>(u, v, uc, vc, ahalf, b, tau);
         const size_t o = off(g, i, j);
         const typename T::V q0 = T::from_d(DFORM ? __dsub_rn(u1, uc) : uc), q1 = T::from_d(u1);
         T::st(L0, o, q0);
         T::st(L1, o, q1);
-        if (PER) {
-            if (!DFORM) write_images<DT>(L0, g, i, j, q0, gw);  // d is read at its own node only
-            write_images<DT>(L1, g, i, j, q1, gw);
+        if (BCM != BCM_ZERO) {
+            if (!DFORM) write_images_bc<DT, BCM>(L0, g, i, j, q0, gw);  // d is read at its own node only
+            write_images_bc<DT, BCM>(L1, g, i, j, q1, gw);
         }
         if (TRACK) error_terms(T::to_d(q1), exact_at(ex, i, j), s0, s1, m0, m1, rd.status);
     }
@@ -50,7 +50,7 @@ __global__ void __launch_bounds__(256) kc1_first_step(const double* __restrict__
 }
 
 // DFORM: `nxt` receives u^{k+1}; `dpl` holds d^k and receives d^{k+1} in place.
-template <int DT, int NC, bool PER, bool TRACK, bool DIFF, bool DFORM>
+template <int DT, int NC, int BCM, bool TRACK, bool DIFF, bool DFORM>
 __global__ void __launch_bounds__(256) kc2_simple(Level cur, Level nxt, Geo g,
                                                   CoefN<typename St<DT>::V, NC> a, ExactTab ex,
                                                   Reduce rd, int gw, Level dpl) {
@@ -72,7 +72,7 @@ __global__ void __launch_bounds__(256) kc2_simple(Level cur, Level nxt, Geo g,
             r = two_step_chain<NC, DIFF>(u, u(0, 0), T::ld(nxt, o), a);
         }
         T::st(nxt, o, r);
-        if (PER) write_images<DT>(nxt, g, i, j, r, gw);
+        if (BCM != BCM_ZERO) write_images_bc<DT, BCM>(nxt, g, i, j, r, gw);
         if (TRACK) error_terms(T::to_d(r), exact_at(ex, i, j), s0, s1, m0, m1, rd.status);
     }
     if (TRACK) reduce_finalize<256>(s0, s1, m0, m1, rd);
@@ -138,7 +138,7 @@ __device__ __forceinline__ ChainRow<T, VEC, H> chain_load_row(const T* row, int 
 
 // DFORM: tm_prev stages d^k; u^{k+1} goes to `nxt`, d^{k+1} to `dout` (in
 // place over d^k, which this tile has already staged).
-template <typename T, int NC, bool PER, int TH, int NW, int NSTAGES, int MINB, bool DIFF, bool DFORM>
+template <typename T, int NC, int BCM, int TH, int NW, int NSTAGES, int MINB, bool DIFF, bool DFORM>
 __global__ void __launch_bounds__(NW * 32, MINB)
     kc2_tma(const __grid_constant__ CUtensorMap tm_cur, const __grid_constant__ CUtensorMap tm_prev,
             T* __restrict__ nxt, Geo g, CoefN<T, NC> a, int tiles_x, int n_tiles, int gw, int* status,
@@ -192,9 +192,9 @@ __global__ void __launch_bounds__(NW * 32, MINB)
         const int x = tx * TW + lane * VEC;
         const int r0 = warp * RPW;
         const int col = HB + lane * VEC;  // this lane's vector inside a staged row
-        const bool edge = PER && (tx * TW < gw || tx * TW + TW > g.nx - gw || ty * TH < gw ||
-                                  ty * TH + TH > g.ny - gw);
-        const bool vec_images = (g.nx % VEC == 0) && g.nx >= 2 * gw && g.ny >= 2 * gw;
+        const bool edge = BCM != BCM_ZERO && (tx * TW < gw || tx * TW + TW > g.nx - gw || ty * TH < gw ||
+                                              ty * TH + TH > g.ny - gw);
+        const bool vec_images = BCM == BCM_PERIODIC && (g.nx % VEC == 0) && g.nx >= 2 * gw && g.ny >= 2 * gw;
 
         // win[q] holds staged row (r + q) of u^k, i.e. grid row y - R + q
         ChainRow<T, VEC, H> win[2 * R + 1];
@@ -261,7 +261,7 @@ __global__ void __launch_bounds__(NW * 32, MINB)
                 if (y >= g.ny) break;
 #pragma unroll 1
                 for (int e = 0; e < VEC; ++e)
-                    if (x + e < g.nx) write_images<DT>(L, g, x + e, y, nxt[off(g, x + e, y)], gw);
+                    if (x + e < g.nx) write_images_bc<DT, BCM>(L, g, x + e, y, nxt[off(g, x + e, y)], gw);
             }
         }
         __syncthreads();  // every warp is done with stage s

@@ -214,18 +214,30 @@ __global__ void __launch_bounds__(NW * 32, 1)
                                out_prev, gw, edge);
 }
 
-// Periodic images of every node within gw of an edge, re-derived from the
-// interior (used once when a handle switches to a mode that reads a deeper
-// ghost ring).
-template <int DT>
+// Images in the first gw ghost rings, re-derived from the interior (used
+// when a handle switches to a mode that reads a deeper ghost ring, and after
+// raw state loads): periodic images, or the odd continuation's negated
+// mirror images (zero on the boundary nodes).
+template <int DT, int BCM>
 __global__ void __launch_bounds__(256) k_refresh_ghosts(Level L, Geo g, int gw) {
     const int W = g.nx + 2 * gw, H = g.ny + 2 * gw;
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < (long long)W * H;
          q += (long long)gridDim.x * blockDim.x) {
         const int ii = (int)(q % W) - gw, jj = (int)(q / W) - gw;
         if (ii >= 0 && ii < g.nx && jj >= 0 && jj < g.ny) continue;
-        const int si = ((ii % g.nx) + g.nx) % g.nx, sj = ((jj % g.ny) + g.ny) % g.ny;
-        St<DT>::st(L, off(g, ii, jj), St<DT>::ld(L, off(g, si, sj)));
+        if constexpr (BCM == BCM_ODD) {
+            double sign = 1.0;
+            const int si = odd_index(ii, g.nx, sign), sj = odd_index(jj, g.ny, sign);
+            if (si < 0 || sj < 0) {
+                St<DT>::st(L, off(g, ii, jj), St<DT>::from_d(0.0));
+            } else {
+                const typename St<DT>::V v = St<DT>::ld(L, off(g, si, sj));
+                St<DT>::st(L, off(g, ii, jj), sign < 0 ? vneg(v) : v);
+            }
+        } else {
+            const int si = ((ii % g.nx) + g.nx) % g.nx, sj = ((jj % g.ny) + g.ny) % g.ny;
+            St<DT>::st(L, off(g, ii, jj), St<DT>::ld(L, off(g, si, sj)));
+        }
     }
 }
 

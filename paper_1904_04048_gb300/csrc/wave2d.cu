@@ -153,6 +153,14 @@ static void dispatch_dt(int dt, Fn&& fn) {
     }
 }
 template <typename Fn>
+static void dispatch_bc(int bc, Fn&& fn) {
+    switch (bc) {
+        case WAVE2D_BC_PERIODIC: fn(IC<BCM_PERIODIC>{}); break;
+        case WAVE2D_BC_ODD: fn(IC<BCM_ODD>{}); break;
+        default: fn(IC<BCM_ZERO>{}); break;
+    }
+}
+template <typename Fn>
 static void dispatch_bool(bool v, Fn&& fn) {
     if (v) fn(BC_<true>{});
     else fn(BC_<false>{});
@@ -314,7 +322,7 @@ static int launch_first_step(wave2d* h, const double* du0, const double* dv0) {
     const Level L0 = h->level(1), L1 = h->level(0);  // u^0 -> plane 1 (u^{k-1}), u^1 -> plane 0
     dispatch_dt(h->dtype, [&](auto DTc) {
         dispatch_s(h->scheme, [&](auto Sc) {
-            dispatch_bool(h->bc == WAVE2D_BC_PERIODIC, [&](auto Pc) {
+            dispatch_bc(h->bc, [&](auto Pc) {
                 dispatch_bool(h->tracking, [&](auto Tc) {
                     k1_first_step<decltype(DTc)::value, decltype(Sc)::value, decltype(Pc)::value,
                                   decltype(Tc)::value><<<grid2d(h), dim3(32, 8), 0, h->stream>>>(
@@ -337,7 +345,7 @@ static int launch_simple_step(wave2d* h, bool track) {
         using V = typename St<DT>::V;
         const Coef3<V> a = coef_as<V>(h->a);
         dispatch_s(h->scheme, [&](auto Sc) {
-            dispatch_bool(h->bc == WAVE2D_BC_PERIODIC, [&](auto Pc) {
+            dispatch_bc(h->bc, [&](auto Pc) {
                 dispatch_bool(track, [&](auto Tc) {
                     k2_simple<DT, decltype(Sc)::value, decltype(Pc)::value, decltype(Tc)::value>
                         <<<grid2d(h), dim3(32, 8), 0, h->stream>>>(cur, nxt, h->geo(), a, ex, rd, h->gw);
@@ -349,11 +357,11 @@ static int launch_simple_step(wave2d* h, bool track) {
     return WAVE2D_OK;
 }
 
-template <typename T, int S, bool PER>
+template <typename T, int S, int BCM>
 static int launch_tma_t(wave2d* h) {
     constexpr int TH = 32;
     using C = TmaCfg<T, S, TH, kTmaNW>;
-    auto kern = k2_tma<T, S, PER, TH, kTmaNW, kTmaStages>;
+    auto kern = k2_tma<T, S, BCM, TH, kTmaNW, kTmaStages>;
     const int smem = 2048 + kTmaStages * C::STAGE_BYTES;
     static thread_local int configured_smem = -1;  // per instantiation
     if (configured_smem != smem) {
@@ -385,8 +393,8 @@ static int launch_tma_step(wave2d* h) {
     int rc = WAVE2D_OK;
     dispatch_s(h->scheme, [&](auto Sc) {
         constexpr int S = decltype(Sc)::value;
-        dispatch_bool(h->bc == WAVE2D_BC_PERIODIC, [&](auto Pc) {
-            constexpr bool P = decltype(Pc)::value;
+        dispatch_bc(h->bc, [&](auto Pc) {
+            constexpr int P = decltype(Pc)::value;
             rc = (h->dtype == DT_F32) ? launch_tma_t<float, S, P>(h) : launch_tma_t<double, S, P>(h);
         });
     });
@@ -463,12 +471,16 @@ static int launch_block(wave2d* h, int64_t remaining) {
 
 // Rewrite the periodic images of the current two levels in the first gw rings.
 static int refresh_ghosts(wave2d* h) {
-    if (h->bc != WAVE2D_BC_PERIODIC || !h->initialized) return WAVE2D_OK;
+    if (h->bc == WAVE2D_BC_ZERO || !h->initialized) return WAVE2D_OK;
     const long long total = (long long)(h->nx + 2 * h->gw) * (h->ny + 2 * h->gw);
     const int grid = (int)std::min<long long>((total + 255) / 256, 8LL * h->num_sms);
     for (int p : {h->cur, h->prv}) {
         dispatch_dt(h->dtype, [&](auto DTc) {
-            k_refresh_ghosts<decltype(DTc)::value><<<grid, 256, 0, h->stream>>>(h->level(p), h->geo(), h->gw);
+            if (h->bc == WAVE2D_BC_ODD)
+                k_refresh_ghosts<decltype(DTc)::value, BCM_ODD><<<grid, 256, 0, h->stream>>>(h->level(p), h->geo(), h->gw);
+            else
+                k_refresh_ghosts<decltype(DTc)::value, BCM_PERIODIC><<<grid, 256, 0, h->stream>>>(h->level(p), h->geo(),
+                                                                                                  h->gw);
         });
         W2D_LAUNCHED("ghost refresh kernel launch");
     }
@@ -493,7 +505,8 @@ static int select_kernel(wave2d* h) {
         want = (h->dtype == DT_F32 && (int64_t)h->nx * h->ny >= 65536) ? WAVE2D_KERNEL_TMA
                                                                        : WAVE2D_KERNEL_SIMPLE;
     }
-    if (want == WAVE2D_KERNEL_TEMPORAL && (h->dtype != DT_F32 || h->nclass > 0)) want = WAVE2D_KERNEL_TMA;
+    if (want == WAVE2D_KERNEL_TEMPORAL && (h->dtype != DT_F32 || h->nclass > 0 || h->bc == WAVE2D_BC_ODD))
+        want = WAVE2D_KERNEL_TMA;
     if (want == WAVE2D_KERNEL_TMA && h->dtype == DT_F32X2) want = WAVE2D_KERNEL_SIMPLE;
     if ((want == WAVE2D_KERNEL_TMA || want == WAVE2D_KERNEL_TEMPORAL) && !h->tma_ready) {
         int rc = prepare_tma(h);
@@ -661,7 +674,7 @@ static void release_handle(wave2d* h) {
 static int check_grid(const wave2d_grid* grid, double hh, double tau, double c, int allowed_flags) {
     if (grid->nx < 1 || grid->ny < 1 || grid->nx > 65536 || grid->ny > 65536)
         return set_error(WAVE2D_ERR_ARG, "grid size %d x %d outside 1..65536", grid->nx, grid->ny);
-    if (grid->bc != WAVE2D_BC_ZERO && grid->bc != WAVE2D_BC_PERIODIC)
+    if (grid->bc != WAVE2D_BC_ZERO && grid->bc != WAVE2D_BC_PERIODIC && grid->bc != WAVE2D_BC_ODD)
         return set_error(WAVE2D_ERR_ARG, "unknown boundary condition %d", grid->bc);
     if (grid->dtype != WAVE2D_F64 && grid->dtype != WAVE2D_F32 && grid->dtype != WAVE2D_F32X2)
         return set_error(WAVE2D_ERR_ARG, "unknown dtype %d", grid->dtype);
@@ -839,6 +852,8 @@ int wave2d_set_tuning(wave2d_t h, const wave2d_tune* tune) {
         return set_error(WAVE2D_ERR_ARG, "unknown kernel %d", tune->kernel);
     if (tune->kernel == WAVE2D_KERNEL_TMA && h->dtype == WAVE2D_F32X2)
         return set_error(WAVE2D_ERR_ARG, "the TMA kernel supports F32 and F64 storage only");
+    if (tune->kernel == WAVE2D_KERNEL_TEMPORAL && h->bc == WAVE2D_BC_ODD)
+        return set_error(WAVE2D_ERR_ARG, "the temporal kernel covers the zero and periodic boundaries");
     if (tune->kernel == WAVE2D_KERNEL_TEMPORAL && h->nclass > 0)
         return set_error(WAVE2D_ERR_ARG,
                          "the temporal kernel covers the 5-, 9- and 13-point schemes with plain sums only");
@@ -1058,7 +1073,7 @@ int wave2d_set_state(wave2d_t h, const double* u_prev, const double* u_cur, int6
     }
     dispatch_dt(h->dtype, [&](auto DTc) {
         constexpr int DT = decltype(DTc)::value;
-        dispatch_bool(h->bc == WAVE2D_BC_PERIODIC, [&](auto Pc) {
+        dispatch_bc(h->bc, [&](auto Pc) {
             k_unpack<DT, decltype(Pc)::value><<<grid2d(h), dim3(32, 8), 0, h->stream>>>(
                 dp, h->level(h->diff_form ? 2 : 1), h->geo(), h->gw);
             k_unpack<DT, decltype(Pc)::value><<<grid2d(h), dim3(32, 8), 0, h->stream>>>(dc, h->level(0), h->geo(), h->gw);
@@ -1141,7 +1156,7 @@ int wave2d_autotune(wave2d_t h, int64_t steps, wave2d_tune* best) {
         t.ctas_per_sm = per_sm;
         cands.push_back(t);
     };
-    if (h->dtype == WAVE2D_F32 && h->nclass > 0) {
+    if (h->dtype == WAVE2D_F32 && (h->nclass > 0 || h->bc == WAVE2D_BC_ODD)) {
         add(WAVE2D_KERNEL_TMA, 0, 0, 1);
         add(WAVE2D_KERNEL_TMA, 0, 0, 2);
         add(WAVE2D_KERNEL_SIMPLE, 0, 0, 0);

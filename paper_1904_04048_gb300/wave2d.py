@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_PKG, "libwave2d.so")
 
 OK = 0
 ERR_ARG, ERR_UNSTABLE, ERR_OOM, ERR_CUDA, ERR_NONFINITE, ERR_TIMEOUT, ERR_STATE = -1, -2, -3, -4, -5, -6, -7
-BC_ZERO, BC_PERIODIC = 0, 1
+BC_ZERO, BC_PERIODIC, BC_ODD = 0, 1, 2
 F64, F32, F32X2 = 0, 1, 2
 ALLOW_UNSTABLE, CONVENTIONAL, DIFF_SUMS, DIFF_FORM = 1, 2, 4, 8
 EXACT_NONE, EXACT_STANDING, EXACT_PLANE = 0, 1, 2
