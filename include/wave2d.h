@@ -148,8 +148,8 @@ typedef struct {
     int32_t kernel;       /* WAVE2D_KERNEL_*                                      */
     int32_t tile_h;       /* output rows per tile of WAVE2D_KERNEL_TEMPORAL: 16,
                              24, 32 or 64; 0 = 32                                 */
-    int32_t temporal_t;   /* steps per launch for WAVE2D_KERNEL_TEMPORAL: 2 or 4;
-                             0 = 4                                                */
+    int32_t temporal_t;   /* steps per launch for WAVE2D_KERNEL_TEMPORAL: 2, 3 or
+                             4; 0 = 4                                             */
     int32_t use_graph;    /* capture runs of steps in a CUDA graph: 1 on, 0 off,
                              -1 automatic                                         */
     int32_t ctas_per_sm;  /* resident CTAs per SM for the TMA kernels; 0 = auto:
@@ -300,7 +300,7 @@ int wave2d_set_tuning(wave2d_t h, const wave2d_tune *tune);
 
 /* Autotuner: time every candidate two-step configuration for `steps` levels
  * on a copy of the current state (FP32: the TMA one-step kernel at 1 and 2
- * CTAs per SM and the temporal kernel with T in {2, 4} and 16, 24, 32 or 64
+ * CTAs per SM and the temporal kernel with T in {2, 3, 4} and 16, 24, 32 or 64
  * rows per tile; derived FP32 schemes: the TMA kernel at 1 and 2 CTAs per SM
  * and the one-node kernel; FP64: TMA at 1 and 2 CTAs per SM and the one-node
  * kernel), restore

@@ -445,6 +445,7 @@ static int launch_temporal(wave2d* h) {
                 }
             };
             if (T == 2) by_oh(IC<2>{});
+            else if (T == 3) by_oh(IC<3>{});
             else by_oh(IC<4>{});
         });
     });
@@ -857,9 +858,8 @@ int wave2d_set_tuning(wave2d_t h, const wave2d_tune* tune) {
     if (tune->kernel == WAVE2D_KERNEL_TEMPORAL && h->nclass > 0)
         return set_error(WAVE2D_ERR_ARG,
                          "the temporal kernel covers the 5-, 9- and 13-point schemes with plain sums only");
-    if (tune->kernel == WAVE2D_KERNEL_TEMPORAL &&
-        !(tune->temporal_t == 0 || tune->temporal_t == 2 || tune->temporal_t == 4))
-        return set_error(WAVE2D_ERR_ARG, "temporal_t must be 0 (auto), 2 or 4 (got %d)", tune->temporal_t);
+    if (tune->kernel == WAVE2D_KERNEL_TEMPORAL && !(tune->temporal_t == 0 || (tune->temporal_t >= 2 && tune->temporal_t <= 4)))
+        return set_error(WAVE2D_ERR_ARG, "temporal_t must be 0 (auto), 2, 3 or 4 (got %d)", tune->temporal_t);
     if (tune->kernel == WAVE2D_KERNEL_TEMPORAL && !(tune->tile_h == 0 || tune->tile_h == 16 ||
                                                     tune->tile_h == 24 || tune->tile_h == 32 || tune->tile_h == 64))
         return set_error(WAVE2D_ERR_ARG, "temporal tile_h must be 0 (auto), 16, 24, 32 or 64 (got %d)", tune->tile_h);
@@ -1163,7 +1163,7 @@ int wave2d_autotune(wave2d_t h, int64_t steps, wave2d_tune* best) {
     } else if (h->dtype == WAVE2D_F32) {
         add(WAVE2D_KERNEL_TMA, 0, 0, 1);
         add(WAVE2D_KERNEL_TMA, 0, 0, 2);
-        for (int T : {2, 4})
+        for (int T : {2, 3, 4})
             for (int oh : {16, 24, 32, 64}) add(WAVE2D_KERNEL_TEMPORAL, oh, T, 0);
     } else if (h->dtype == WAVE2D_F64) {
         add(WAVE2D_KERNEL_TMA, 0, 0, 1);

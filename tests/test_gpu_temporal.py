@@ -44,13 +44,13 @@ def run(w, scheme, u0, v0, h, lam, steps, bc, tune, chunks=None):
 
 @pytest.mark.parametrize("scheme", [5, 9, 13])
 @pytest.mark.parametrize("bc", [BC_ZERO, BC_PERIODIC], ids=["zero", "periodic"])
-@pytest.mark.parametrize("T,oh", [(2, 32), (2, 64), (4, 32), (4, 64)])
+@pytest.mark.parametrize("T,oh", [(2, 32), (2, 64), (3, 24), (3, 32), (4, 16), (4, 24), (4, 32), (4, 64)])
 @pytest.mark.parametrize("shape", SIZES, ids=lambda s: f"{s[0]}x{s[1]}")
 def test_temporal_equals_single_steps_bitwise(w, scheme, bc, T, oh, shape):
     nx, ny = shape
     u0, v0, h = smooth_ic(nx, ny, bc, seed=nx + ny + T)
     lam = 0.9 * LAMBDA_MAX[scheme]
-    steps = 38  # 37 two-steps: not a multiple of T
+    steps = 38  # 37 two-steps: not a multiple of 2, 3 or 4
     ref = run(w, scheme, u0, v0, h, lam, steps, bc, dict(kernel=w.KERNEL_TMA, use_graph=0))
     got = run(w, scheme, u0, v0, h, lam, steps, bc,
               dict(kernel=w.KERNEL_TEMPORAL, temporal_t=T, tile_h=oh, use_graph=0))
