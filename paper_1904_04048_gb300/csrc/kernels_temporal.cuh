@@ -85,7 +85,7 @@ __device__ __forceinline__ void region_advance(float* Q, float* P, int RH, int g
             Row4 win[2 * R + 1];
 #pragma unroll
             for (int q = 1; q < 2 * R + 1; ++q) win[q] = smem_row4(src + (r0 - R + q - 1) * RW, lp_i, v_i, rp_i);
-#pragma unroll 2
+#pragma unroll 4
             for (int r = r0; r < r1; ++r) {
 #pragma unroll
                 for (int q = 0; q < 2 * R; ++q) win[q] = win[q + 1];
