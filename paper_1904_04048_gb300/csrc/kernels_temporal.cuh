@@ -59,6 +59,7 @@ template <int S, bool PER, int RVW, int T, int NW>
 __device__ __forceinline__ void region_advance(float* Q, float* P, int RH, int gx0, int gy0, const Geo& g,
                                                const Coef3<float>& a) {
     constexpr int R = (S == 13) ? 2 : 1, RW = 4 * RVW, WPR = RVW / 32, NRG = NW / WPR;
+    constexpr int UNROLL = (S == 13) ? 8 : 4;  // rows walked per unrolled step
     static_assert(NW % WPR == 0, "warps per row group");
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int vidx = (warp % WPR) * 32 + lane;  // region vector owned by this thread
@@ -85,7 +86,7 @@ __device__ __forceinline__ void region_advance(float* Q, float* P, int RH, int g
             Row4 win[2 * R + 1];
 #pragma unroll
             for (int q = 1; q < 2 * R + 1; ++q) win[q] = smem_row4(src + (r0 - R + q - 1) * RW, lp_i, v_i, rp_i);
-#pragma unroll 4
+#pragma unroll UNROLL
             for (int r = r0; r < r1; ++r) {
 #pragma unroll
                 for (int q = 0; q < 2 * R; ++q) win[q] = win[q + 1];
