@@ -52,9 +52,9 @@ FP32_OPS = {5: 9, 9: 14, 13: 19}
 # from an ncu capture of the same kernel source (see the profiles directory),
 # keyed by (kernel, hash of the kernel sources, scheme, tile rows) so that a
 # figure is dropped once the kernel or the autotuner's choice changes.
-NCU_TRAFFIC = {("k3_temporal", "92440fad3f09d537", 13, 32): 136017664 + 88732160,
-               ("k3_temporal", "92440fad3f09d537", 9, 24): 135961600 + 87288320,
-               ("k2_tma", "92440fad3f09d537", 13, 0): 135368192 + 20378880}
+NCU_TRAFFIC = {("k3_temporal", "b20aeb2c8a3d08a2", 13, 32): 135976448 + 88738560,
+               ("k3_temporal", "b20aeb2c8a3d08a2", 9, 24): 135962880 + 87939328,
+               ("k2_tma", "b20aeb2c8a3d08a2", 13, 0): 135368704 + 19907584}
 
 # The autotuner's choice on GB300 (temporal kernel, T = 4, rows per tile),
 # used by --fixed-tuning for profiler runs.
