@@ -386,7 +386,7 @@ def run_ours(args, rank, world, local_rank):
         "result_norms": {str(s): [results[s][0], results[s][1]] for s in SCHEMES},
     }
     if world == 1 and not args.no_extras:
-        line["config1"] = measure_config1(w, torch)
+        line["fp64_5point_256"] = measure_small_fp64(w, torch)
         line["batched"] = measure_batched(w, torch)
         line["served"] = measure_served(w, torch)
         line["derived_schemes"] = measure_derived(w, torch, u0, v0, peak)
@@ -508,7 +508,7 @@ def measure_served(w, torch):
             "latency": "submission to norms on the host (library steady clock)"}
 
 
-def measure_config1(w, torch):
+def measure_small_fp64(w, torch):
     """5-point scheme, FP64, 256^2, h = 1/256, c = 1, lambda = 0.5, 200 time
     levels, centred Gaussian pulse (sigma 0.05), v0 = 0, zero boundary: wall
     time of one whole run (first step, 199 two-steps in a CUDA graph, FP64
