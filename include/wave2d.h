@@ -95,7 +95,7 @@ enum {
                                   longest waves need WAVE2D_DIFF_FORM).  F32 and
                                   F64 storage; one-node and TMA kernels only (no
                                   temporal blocking, no batches).                */
-    WAVE2D_DIFF_FORM = 8       /* F32 only: keep u^k and d^k = u^k - u^{k-1} and
+    WAVE2D_DIFF_FORM = 8,      /* F32 only: keep u^k and d^k = u^k - u^{k-1} and
                                   step d^{k+1} = d^k + Lambda(u^k),
                                   u^{k+1} = u^k + d^{k+1} (the same recursion,
                                   Eq. A2) with difference sums: the rounding of
@@ -104,6 +104,13 @@ enum {
                                   one-node and TMA kernels.  get/set_state
                                   convert to and from (u^{k-1}, u^k) in FP64;
                                   the raw layout is [d^k][u^k].                 */
+    WAVE2D_CANARY = 16         /* debug: fill the plane cells no one-level kernel
+                                  writes and no result depends on (ghost cells
+                                  more than R rows or R + 4 columns outside the
+                                  grid, row padding) with a NaN pattern;
+                                  wave2d_canary_check counts cells that changed.
+                                  Such handles do not use the temporal kernel or
+                                  batches (they use the whole ring).             */
 };
 
 /* Exact solutions for wave2d_error_vs_exact / wave2d_track_error.
@@ -320,6 +327,13 @@ int wave2d_sync(wave2d_t h);
  * which the next synchronising call (wave2d_sync, norms, state) reports as
  * WAVE2D_ERR_TIMEOUT and clears; the GPU stays usable. */
 int wave2d_selftest_timeout(wave2d_t h, int64_t limit_cycles);
+
+/* Guard-band check of a handle created with WAVE2D_CANARY: *changed receives
+ * the number of canary cells (see WAVE2D_CANARY) whose bits differ from the
+ * pattern written at create and after wave2d_set_raw — 0 unless a kernel
+ * wrote outside the part of the planes it owns.  Synchronises the stream.
+ * WAVE2D_ERR_STATE for a handle without the flag. */
+int wave2d_canary_check(wave2d_t h, int64_t *changed);
 void wave2d_destroy(wave2d_t h);
 const char *wave2d_last_error(void);
 

@@ -466,6 +466,8 @@ int wave2d_batch_create(wave2d_t* handles, int n, const wave2d_tune* opt, wave2d
     for (int i = 0; i < n; ++i) {
         if (!handles[i]) return set_error(WAVE2D_ERR_ARG, "null handle %d", i);
         if (handles[i]->dtype != WAVE2D_F32) return set_error(WAVE2D_ERR_ARG, "batched stepping needs F32 storage");
+        if (handles[i]->flags & WAVE2D_CANARY)
+            return set_error(WAVE2D_ERR_ARG, "handles with guard-band canaries are not batched");
         if (handles[i]->bc == WAVE2D_BC_ODD)
             return set_error(WAVE2D_ERR_ARG, "batched stepping covers the zero and periodic boundaries");
         if (handles[i]->nclass > 0)

@@ -506,7 +506,8 @@ static int select_kernel(wave2d* h) {
         want = (h->dtype == DT_F32 && (int64_t)h->nx * h->ny >= 65536) ? WAVE2D_KERNEL_TMA
                                                                        : WAVE2D_KERNEL_SIMPLE;
     }
-    if (want == WAVE2D_KERNEL_TEMPORAL && (h->dtype != DT_F32 || h->nclass > 0 || h->bc == WAVE2D_BC_ODD))
+    if (want == WAVE2D_KERNEL_TEMPORAL &&
+        (h->dtype != DT_F32 || h->nclass > 0 || h->bc == WAVE2D_BC_ODD || (h->flags & WAVE2D_CANARY)))
         want = WAVE2D_KERNEL_TMA;
     if (want == WAVE2D_KERNEL_TMA && h->dtype == DT_F32X2) want = WAVE2D_KERNEL_SIMPLE;
     if ((want == WAVE2D_KERNEL_TMA || want == WAVE2D_KERNEL_TEMPORAL) && !h->tma_ready) {
@@ -744,6 +745,8 @@ static int create_device_state(wave2d* h, const wave2d_grid* grid) {
     h->tab_track = (double*)p;
     e = cudaMemsetAsync(h->base, 0, h->base_bytes, h->stream);
     if (e != cudaSuccess) return cuda_fail(e, "memset");
+    int rc = canary_fill(h);
+    if (rc != WAVE2D_OK) return rc;
     return select_kernel(h);
 }
 
@@ -766,7 +769,8 @@ int wave2d_create(const wave2d_grid* grid, double hh, double tau, double c, int 
     if (scheme != 5 && scheme != 9 && scheme != 13)
         return set_error(WAVE2D_ERR_ARG, "scheme must be 5, 9 or 13 (got %d)", scheme);
     int rc = check_grid(grid, hh, tau, c,
-                        WAVE2D_ALLOW_UNSTABLE | WAVE2D_CONVENTIONAL | WAVE2D_DIFF_SUMS | WAVE2D_DIFF_FORM);
+                        WAVE2D_ALLOW_UNSTABLE | WAVE2D_CONVENTIONAL | WAVE2D_DIFF_SUMS | WAVE2D_DIFF_FORM |
+                            WAVE2D_CANARY);
     if (rc != WAVE2D_OK) return rc;
     const bool conventional = (grid->flags & WAVE2D_CONVENTIONAL) != 0;
     const double lam = c * tau / hh;
@@ -810,7 +814,7 @@ int wave2d_create_scheme(const wave2d_grid* grid, double hh, double tau, double 
     *out = nullptr;
     int rc = check_scheme(s);
     if (rc != WAVE2D_OK) return rc;
-    rc = check_grid(grid, hh, tau, c, WAVE2D_ALLOW_UNSTABLE | WAVE2D_DIFF_SUMS | WAVE2D_DIFF_FORM);
+    rc = check_grid(grid, hh, tau, c, WAVE2D_ALLOW_UNSTABLE | WAVE2D_DIFF_SUMS | WAVE2D_DIFF_FORM | WAVE2D_CANARY);
     if (rc != WAVE2D_OK) return rc;
     const double lam = c * tau / hh;
     const double lmax = scheme_lambda_max(s);
@@ -853,6 +857,8 @@ int wave2d_set_tuning(wave2d_t h, const wave2d_tune* tune) {
         return set_error(WAVE2D_ERR_ARG, "unknown kernel %d", tune->kernel);
     if (tune->kernel == WAVE2D_KERNEL_TMA && h->dtype == WAVE2D_F32X2)
         return set_error(WAVE2D_ERR_ARG, "the TMA kernel supports F32 and F64 storage only");
+    if (tune->kernel == WAVE2D_KERNEL_TEMPORAL && (h->flags & WAVE2D_CANARY))
+        return set_error(WAVE2D_ERR_ARG, "handles with guard-band canaries do not use the temporal kernel");
     if (tune->kernel == WAVE2D_KERNEL_TEMPORAL && h->bc == WAVE2D_BC_ODD)
         return set_error(WAVE2D_ERR_ARG, "the temporal kernel covers the zero and periodic boundaries");
     if (tune->kernel == WAVE2D_KERNEL_TEMPORAL && h->nclass > 0)
@@ -1138,6 +1144,8 @@ int wave2d_set_raw(wave2d_t h, const void* src, int64_t bytes, int64_t k) {
     h->k = k;
     h->initialized = true;
     drop_graphs(h);
+    int rc = canary_fill(h);  // the copied planes carry the source's guard band
+    if (rc != WAVE2D_OK) return rc;
     return refresh_ghosts(h);  // the copied rings may come from a shallower mode
 }
 
@@ -1156,7 +1164,7 @@ int wave2d_autotune(wave2d_t h, int64_t steps, wave2d_tune* best) {
         t.ctas_per_sm = per_sm;
         cands.push_back(t);
     };
-    if (h->dtype == WAVE2D_F32 && (h->nclass > 0 || h->bc == WAVE2D_BC_ODD)) {
+    if (h->dtype == WAVE2D_F32 && (h->nclass > 0 || h->bc == WAVE2D_BC_ODD || (h->flags & WAVE2D_CANARY))) {
         add(WAVE2D_KERNEL_TMA, 0, 0, 1);
         add(WAVE2D_KERNEL_TMA, 0, 0, 2);
         add(WAVE2D_KERNEL_SIMPLE, 0, 0, 0);

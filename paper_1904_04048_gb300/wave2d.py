@@ -21,7 +21,7 @@ OK = 0
 ERR_ARG, ERR_UNSTABLE, ERR_OOM, ERR_CUDA, ERR_NONFINITE, ERR_TIMEOUT, ERR_STATE = -1, -2, -3, -4, -5, -6, -7
 BC_ZERO, BC_PERIODIC, BC_ODD = 0, 1, 2
 F64, F32, F32X2 = 0, 1, 2
-ALLOW_UNSTABLE, CONVENTIONAL, DIFF_SUMS, DIFF_FORM = 1, 2, 4, 8
+ALLOW_UNSTABLE, CONVENTIONAL, DIFF_SUMS, DIFF_FORM, CANARY = 1, 2, 4, 8, 16
 EXACT_NONE, EXACT_STANDING, EXACT_PLANE = 0, 1, 2
 KERNEL_AUTO, KERNEL_SIMPLE, KERNEL_TMA, KERNEL_TEMPORAL = 0, 1, 2, 3
 
@@ -129,6 +129,7 @@ SIGNATURES = {
     "wave2d_get_info": (ctypes.c_int, [_P, ctypes.POINTER(wave2d_info_t)]),
     "wave2d_sync": (ctypes.c_int, [_P]),
     "wave2d_selftest_timeout": (ctypes.c_int, [_P, ctypes.c_int64]),
+    "wave2d_canary_check": (ctypes.c_int, [_P, _I64P]),
     "wave2d_destroy": (None, [_P]),
     "wave2d_last_error": (ctypes.c_char_p, []),
     "wave2d_launch_count": (ctypes.c_int64, []),
@@ -372,6 +373,12 @@ class Wave2D:
         inf = wave2d_info_t()
         check(lib().wave2d_get_info(self._h, ctypes.byref(inf)))
         return inf
+
+    def canary_check(self) -> int:
+        """Number of guard-band cells that changed (handles with CANARY)."""
+        out = ctypes.c_int64()
+        check(lib().wave2d_canary_check(self._h, ctypes.byref(out)))
+        return out.value
 
     def sync(self):
         check(lib().wave2d_sync(self._h))
