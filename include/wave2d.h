@@ -143,7 +143,10 @@ typedef struct {
 
 typedef struct wave2d *wave2d_t;
 
-/* Kernel selection for the two-step.  Zero-initialised = automatic. */
+/* Kernel selection for the two-step.  Zero-initialised = automatic: the
+ * one-node kernel below 65536 nodes and for FP64 / FP32x2, the TMA kernel for
+ * FP32, and from 2^20 nodes the temporal kernel (T = 4) for the FP32 Section 6
+ * schemes on the zero and periodic boundaries. */
 enum {
     WAVE2D_KERNEL_AUTO = 0,
     WAVE2D_KERNEL_SIMPLE = 1,   /* one thread per node, global loads            */

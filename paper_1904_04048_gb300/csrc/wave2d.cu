@@ -500,11 +500,16 @@ static void drop_graphs(wave2d* h) {
 static int select_kernel(wave2d* h) {
     int want = h->tune.kernel;
     if (want == WAVE2D_KERNEL_AUTO) {
-        // FP32: TMA tiles once the grid fills the GPU.  FP64 and FP32x2 are
+        // FP32: TMA tiles once the grid fills the GPU, and from 2^20 nodes the
+        // temporally blocked kernel where it applies (measured faster at
+        // 4096^2 and 8192^2 for every Section 6 scheme).  FP64 and FP32x2 are
         // bound by arithmetic on GB300 (measured: the one-node kernel is as
         // fast at 4096^2 and 2.4x faster at 256^2), so they keep it.
-        want = (h->dtype == DT_F32 && (int64_t)h->nx * h->ny >= 65536) ? WAVE2D_KERNEL_TMA
-                                                                       : WAVE2D_KERNEL_SIMPLE;
+        const int64_t nodes = (int64_t)h->nx * h->ny;
+        const bool temporal_ok = h->nclass == 0 && h->bc != WAVE2D_BC_ODD && !(h->flags & WAVE2D_CANARY);
+        want = (h->dtype != DT_F32 || nodes < 65536) ? WAVE2D_KERNEL_SIMPLE
+               : (temporal_ok && nodes >= (1 << 20)) ? WAVE2D_KERNEL_TEMPORAL
+                                                     : WAVE2D_KERNEL_TMA;
     }
     if (want == WAVE2D_KERNEL_TEMPORAL &&
         (h->dtype != DT_F32 || h->nclass > 0 || h->bc == WAVE2D_BC_ODD || (h->flags & WAVE2D_CANARY)))
@@ -516,7 +521,9 @@ static int select_kernel(wave2d* h) {
     }
     if (want == WAVE2D_KERNEL_TEMPORAL) {
         h->temporal_t = h->tune.temporal_t > 0 ? h->tune.temporal_t : 4;
-        h->temporal_oh = h->tune.tile_h > 0 ? h->tune.tile_h : 32;
+        // default tile rows: the autotuner's choice on GB300 (3 CTAs per SM for
+        // the 9-point scheme, 2 for the others)
+        h->temporal_oh = h->tune.tile_h > 0 ? h->tune.tile_h : (h->scheme == 9 ? 24 : 32);
         int rc = prepare_temporal(h);
         if (rc != WAVE2D_OK) return rc;
     }

@@ -43,7 +43,7 @@ def test_benchmark_inputs_against_oracle(w, orc, bench_ic, scheme):
     lam = 0.9 * LAMBDA_MAX[scheme]
     steps = 10
     with w.Wave2D(N, N, h, lam * h, scheme=scheme, bc=BC_PERIODIC, dtype=1) as sim:
-        assert sim.info().kernel == w.KERNEL_TMA  # automatic choice at this size
+        assert sim.info().kernel == w.KERNEL_TEMPORAL  # automatic choice at this size
         sim.first_step(u0, v0)
         sim.step_n(steps - 1)
         up, uc, _ = sim.get_state()
