@@ -18,6 +18,7 @@
 #include <cmath>
 #include <cstring>
 #include <numeric>
+#include <type_traits>
 #include <vector>
 
 #include "kernels_temporal.cuh"
@@ -43,11 +44,18 @@ struct BatchInst {
 template <int S, bool PER>
 __device__ __forceinline__ void batch_advance(float* Q, float* P, int Ti, int rh, int gx0, int gy0, const Geo& g,
                                               const Coef3<float>& a) {
+    // the lane widths of the single-grid temporal kernel: two columns per lane
+    // for radius-1 schemes, four for the 13-point scheme
+    auto adv = [&](auto Tc) {
+        constexpr int TT = decltype(Tc)::value;
+        if constexpr (S == 13) region_advance<S, PER, kBatchRVW, TT, kBatchNW>(Q, P, rh, gx0, gy0, g, a);
+        else region_advance2<S, PER, kBatchRVW, TT, kBatchNW>(Q, P, rh, gx0, gy0, g, a);
+    };
     switch (Ti) {
-        case 1: region_advance<S, PER, kBatchRVW, 1, kBatchNW>(Q, P, rh, gx0, gy0, g, a); break;
-        case 2: region_advance<S, PER, kBatchRVW, 2, kBatchNW>(Q, P, rh, gx0, gy0, g, a); break;
-        case 3: region_advance<S, PER, kBatchRVW, 3, kBatchNW>(Q, P, rh, gx0, gy0, g, a); break;
-        default: region_advance<S, PER, kBatchRVW, 4, kBatchNW>(Q, P, rh, gx0, gy0, g, a); break;
+        case 1: adv(std::integral_constant<int, 1>{}); break;
+        case 2: adv(std::integral_constant<int, 2>{}); break;
+        case 3: adv(std::integral_constant<int, 3>{}); break;
+        default: adv(std::integral_constant<int, 4>{}); break;
     }
 }
 
