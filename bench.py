@@ -52,9 +52,9 @@ FP32_OPS = {5: 9, 9: 14, 13: 19}
 # from an ncu capture of the same kernel source (see the profiles directory),
 # keyed by (kernel, hash of the kernel sources, scheme, tile rows) so that a
 # figure is dropped once the kernel or the autotuner's choice changes.
-NCU_TRAFFIC = {("k3_temporal", "b20aeb2c8a3d08a2", 13, 32): 135976448 + 88738560,
-               ("k3_temporal", "b20aeb2c8a3d08a2", 9, 24): 135962880 + 87939328,
-               ("k2_tma", "b20aeb2c8a3d08a2", 13, 0): 135368704 + 19907584}
+NCU_TRAFFIC = {("k3_temporal", "5a15dac999df3c2c", 13, 32): 135976448 + 88614656,
+               ("k3_temporal", "5a15dac999df3c2c", 9, 24): 135993600 + 87811584,
+               ("k2_tma", "5a15dac999df3c2c", 13, 0): 135366144 + 19802368}
 
 # The autotuner's choice on GB300 (temporal kernel, T = 4, rows per tile),
 # used by --fixed-tuning for profiler runs.
