@@ -48,6 +48,9 @@ WORKLOAD = ("9-point + 13-point schemes, FP32 storage, 4096^2 periodic grid, lam
 # coefficients, and 2 u^k - u^{k-1} + Lambda.
 FP32_OPS = {5: 9, 9: 14, 13: 19}
 
+# Kernel names by WAVE2D_KERNEL_* value (the profiles use the same names).
+KNAME = {1: "k2_simple", 2: "k2_tma", 3: "k3_temporal", 4: "k5_stream"}
+
 # DRAM bytes (read + write) of one launch of a kernel at the benchmark size,
 # from an ncu capture of the same kernel source (see the profiles directory),
 # keyed by (kernel, hash of the kernel sources, scheme, tile rows) so that a
@@ -56,14 +59,14 @@ NCU_TRAFFIC = {("k3_temporal", "5a15dac999df3c2c", 13, 32): 135976448 + 88614656
                ("k3_temporal", "5a15dac999df3c2c", 9, 24): 135993600 + 87811584,
                ("k2_tma", "5a15dac999df3c2c", 13, 0): 135366144 + 19802368}
 
-# The autotuner's choice on GB300 (temporal kernel, T = 4, rows per tile),
+# The autotuner's choice on GB300 (kernel, T = 4, rows per tile or strip),
 # used by --fixed-tuning for profiler runs.
-FIXED_TILE = {9: 24, 13: 32}
+FIXED_TUNING = {9: ("stream", 16), 13: ("stream", 32)}
 
 
 def kernel_source_hash() -> str:
     hsh = hashlib.sha256()
-    for f in ("kernels.cuh", "kernels_temporal.cuh", "stencil_ops.cuh"):
+    for f in ("kernels.cuh", "kernels_temporal.cuh", "kernels_stream.cuh", "stencil_ops.cuh"):
         with open(os.path.join(ROOT, "paper_1904_04048_gb300", "csrc", f), "rb") as fh:
             hsh.update(fh.read())
     return hsh.hexdigest()[:16]
@@ -209,14 +212,13 @@ def run_ours(args, rank, world, local_rank):
     for s in SCHEMES:
         sims[s].first_step(du0, dv0)
         if args.fixed_tuning:  # the autotuner's choice on the measured runs
-            sims[s].set_tuning(kernel=w.KERNEL_TEMPORAL, temporal_t=4, tile_h=FIXED_TILE[s])
-            best = w.wave2d_tune(w.KERNEL_TEMPORAL, FIXED_TILE[s], 4, -1, 0)
+            kern = w.KERNEL_STREAM if FIXED_TUNING[s][0] == "stream" else w.KERNEL_TEMPORAL
+            sims[s].set_tuning(kernel=kern, temporal_t=4, tile_h=FIXED_TUNING[s][1])
+            best = w.wave2d_tune(kern, FIXED_TUNING[s][1], 4, -1, 0)
         else:
             best = sims[s].autotune(steps=64)
-        tuned[s] = {"kernel": {1: "simple", 2: "tma", 3: "temporal"}[best.kernel],
+        tuned[s] = {"kernel": {1: "simple", 2: "tma", 3: "temporal", 4: "stream"}[best.kernel],
                     "temporal_t": best.temporal_t, "tile_h": best.tile_h, "ctas_per_sm": best.ctas_per_sm}
-    kernel = sims[13].info().kernel
-    T13 = sims[13].info().temporal_t
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 512 MiB > L2
     torch.cuda.synchronize(dev)
     results = {}
@@ -272,16 +274,18 @@ def run_ours(args, rank, world, local_rank):
         return e0.elapsed_time(e1) / 1e3
 
     # Per-launch durations of the kernels inside step_n (after the timed
-    # region): the one-step TMA kernel, and the temporal kernel if chosen.
+    # region): the one-step TMA kernel that finishes runs of a multi-level
+    # kernel (temporal or streaming), and which kernel each handle uses.
+    MULTI = (w.KERNEL_TEMPORAL, w.KERNEL_STREAM)
+    kinfo = {}
     one_step = {}
     for s in SCHEMES:
         info = sims[s].info()
-        if info.kernel == w.KERNEL_TEMPORAL:
-            T = info.temporal_t
-            saved = (info.kernel, info.temporal_t)
+        kinfo[s] = (info.kernel, info.temporal_t)
+        if info.kernel in MULTI:
             sims[s].set_tuning(kernel=w.KERNEL_TMA, use_graph=0)
             one_step[s] = time_levels(sims[s], 200) / 200
-            sims[s].set_tuning(kernel=w.KERNEL_TEMPORAL, temporal_t=saved[1], tile_h=tuned[s]["tile_h"])
+            sims[s].set_tuning(kernel=info.kernel, temporal_t=info.temporal_t, tile_h=tuned[s]["tile_h"])
         else:
             one_step[s] = None
 
@@ -313,53 +317,58 @@ def run_ours(args, rank, world, local_rank):
     peak, peak_src = measured_peaks()
     src_hash = kernel_source_hash()
     per_scheme_stepn = {s: sum(a.elapsed_time(b) for ss, a, b in timing if ss == s) / 1e3 for s in SCHEMES}
-    if kernel == w.KERNEL_TEMPORAL:
-        # step_n(1999) = floor(1999/T) temporal launches + (1999 mod T) one-step launches
-        T = T13
-        n_temp = args.steps * len(SCHEMES) * ((STEPS_PER_SCHEME - 1) // T)
-        n_single = args.steps * len(SCHEMES) * ((STEPS_PER_SCHEME - 1) % T)
-        single_s = sum(args.steps * ((STEPS_PER_SCHEME - 1) % T) * (one_step[s] or 0.0) for s in SCHEMES)
-        avg_launch = (stepn_s - single_s) / n_temp
-        alg_bytes = 16 * N * N  # per launch: read u^k, u^{k-1}; write u^{k+T}, u^{k+T-1} (FP32)
-        kname = f"k3_temporal (FP32, T={T}, 9/13-point)"
-        effective = 12 * T * N * N / avg_launch / 1e9  # bytes the one-step kernels would move
-    else:
-        T = 1
-        avg_launch = stepn_s / (args.steps * len(SCHEMES) * (STEPS_PER_SCHEME - 1))
-        alg_bytes = 12 * N * N  # read u^k, read u^{k-1}, write u^{k+1} (FP32)
-        kname = "k2_tma (two-step, FP32, 9/13-point)"
-        effective = alg_bytes / avg_launch / 1e9
-    achieved = alg_bytes / avg_launch / 1e9
-    if kernel == w.KERNEL_TEMPORAL:
-        per = [NCU_TRAFFIC.get(("k3_temporal", src_hash, s, tuned[s]["tile_h"])) for s in SCHEMES]
-    else:
-        per = [NCU_TRAFFIC.get(("k2_tma", src_hash, s, 0)) for s in SCHEMES]
-    traffic = int(sum(per) / len(per)) if all(per) else None  # mean over the schemes' launches
     clocks = clk.summary()
-    hbm_view = {"bound": "hbm", "kernel": kname, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "peak_source": peak_src,
-                "algorithmic_bytes_per_launch": alg_bytes, "levels_per_launch": T,
-                "avg_launch_us": round(avg_launch * 1e6, 3), "traffic": traffic,
-                "unblocked_equivalent_gbs": round(effective, 1)}
-    if kernel == w.KERNEL_TEMPORAL:
-        # Temporal blocking takes the kernel off HBM (DRAM about 26 % busy in
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = clocks.get("sm_max_mhz") or 2070.0
+    alu_peak = sms * 128 * mhz * 1e6 / 1e12
+    # One roofline per kernel in step_n, over the launches of the schemes that
+    # use it.  step_n(1999) of a multi-level kernel = floor(1999 / T) launches
+    # of T levels + (1999 mod T) one-step launches (timed separately above).
+    groups = {}
+    for s in SCHEMES:
+        kern, T = kinfo[s]
+        if kern not in MULTI:
+            T = 1
+        groups.setdefault((KNAME[kern], T), []).append(s)
+    rooflines = []
+    for (kname, T), ss in groups.items():
+        total = sum(per_scheme_stepn[s] for s in ss)
+        if T > 1:
+            total -= sum(args.steps * ((STEPS_PER_SCHEME - 1) % T) * one_step[s] for s in ss)
+        n_launch = len(ss) * args.steps * ((STEPS_PER_SCHEME - 1) // T)
+        avg_launch = total / n_launch
+        alg_bytes = (16 if T > 1 else 12) * N * N  # read the two levels, write two (one for one step)
+        achieved = alg_bytes / avg_launch / 1e9
+        per = [NCU_TRAFFIC.get((kname, src_hash, s, tuned[s]["tile_h"] if T > 1 else 0)) for s in ss]
+        traffic = int(sum(per) / len(per)) if all(per) else None  # mean over the schemes' launches
+        label = f"{kname} (FP32, T={T}, {'/'.join(str(s) for s in ss)}-point)"
+        hbm_view = {"bound": "hbm", "kernel": label, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                    "frac": round(achieved / peak, 4), "peak_source": peak_src,
+                    "algorithmic_bytes_per_launch": alg_bytes, "levels_per_launch": T,
+                    "avg_launch_us": round(avg_launch * 1e6, 3), "traffic": traffic,
+                    "unblocked_equivalent_gbs": round(12 * T * N * N / avg_launch / 1e9, 1),
+                    "share_of_step_n": round(sum(per_scheme_stepn[s] for s in ss) / stepn_s, 4)}
+        if T == 1:
+            rooflines.append(hbm_view)
+            continue
+        # Temporal blocking takes the kernel off HBM (DRAM 31-44 % busy in
         # ncu); its limit is the FP32 pipe.  Algorithmic work: the two-step as
-        # written, FP32_OPS per node-update, T levels per launch, the two
-        # schemes' launches equally many.  Peak: one FP32 add, multiply or
-        # fused multiply-add per lane per clock, 128 lanes per SM.
-        sms = torch.cuda.get_device_properties(dev).multi_processor_count
-        mhz = clocks.get("sm_max_mhz") or 2070.0
-        alu_peak = sms * 128 * mhz * 1e6 / 1e12
-        alg_ops = T * N * N * sum(FP32_OPS[s] for s in SCHEMES) / len(SCHEMES)
+        # written, FP32_OPS per node-update, T levels per launch, the schemes'
+        # launches equally many.  Peak: one FP32 add, multiply or fused
+        # multiply-add per lane per clock, 128 lanes per SM.
+        alg_ops = T * N * N * sum(FP32_OPS[s] for s in ss) / len(ss)
         alu = alg_ops / avg_launch / 1e12
-        roofline = {"bound": "alu", "kernel": kname, "achieved": round(alu, 2), "peak": round(alu_peak, 2),
-                    "unit": "TFLOP/s", "frac": round(alu / alu_peak, 4),
-                    "flop": "one FP32 add, multiply or fused multiply-add (one FP32-pipe lane slot)",
-                    "peak_source": f"{sms} SMs x 128 FP32 lanes x {mhz:.0f} MHz (maximum SM clock)",
-                    "algorithmic_flop_per_launch": int(alg_ops), "levels_per_launch": T,
-                    "avg_launch_us": round(avg_launch * 1e6, 3), "traffic": traffic, "hbm": hbm_view}
-    else:
-        roofline = hbm_view
+        rooflines.append({"bound": "alu", "kernel": label, "achieved": round(alu, 2), "peak": round(alu_peak, 2),
+                          "unit": "TFLOP/s", "frac": round(alu / alu_peak, 4),
+                          "flop": "one FP32 add, multiply or fused multiply-add (one FP32-pipe lane slot)",
+                          "peak_source": f"{sms} SMs x 128 FP32 lanes x {mhz:.0f} MHz (maximum SM clock)",
+                          "algorithmic_flop_per_launch": int(alg_ops), "levels_per_launch": T,
+                          "avg_launch_us": round(avg_launch * 1e6, 3), "traffic": traffic,
+                          "share_of_step_n": hbm_view["share_of_step_n"], "hbm": hbm_view})
+    rooflines.sort(key=lambda r: -r["share_of_step_n"])
+    roofline = dict(rooflines[0])  # the dominant kernel
+    if len(rooflines) > 1:
+        roofline["other_kernels"] = rooflines[1:]
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": "G point-updates/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(elapsed / args.steps * 1e3, 3),
@@ -614,6 +623,7 @@ def profile_case(kernel: str, scheme: int, segment: int = 28, tile_h: int = 32):
     0.5 GB on the device.
       k2_tma:      4 one-step launches (the first step comes before them)
       k3_temporal: 3 launches of T = 4 levels, tile_h-row tiles
+      k5_stream:   3 launches of T = 4 levels, tile_h-row strips
       kc2_tma:     4 one-step launches of a derived scheme (``segment``)"""
     from initial_data import BC_PERIODIC, LAMBDA_MAX, pulses_and_noise
     from paper_1904_04048_gb300 import wave2d as w
@@ -628,6 +638,9 @@ def profile_case(kernel: str, scheme: int, segment: int = 28, tile_h: int = 32):
         if kernel in ("k2_tma", "kc2_tma"):
             sim.set_tuning(kernel=w.KERNEL_TMA, use_graph=0)
             levels = 4
+        elif kernel == "k5_stream":
+            sim.set_tuning(kernel=w.KERNEL_STREAM, temporal_t=4, tile_h=tile_h, use_graph=0)
+            levels = 12
         else:
             sim.set_tuning(kernel=w.KERNEL_TEMPORAL, temporal_t=4, tile_h=tile_h, use_graph=0)
             levels = 12
@@ -683,9 +696,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the batched and served workloads")
     ap.add_argument("--fixed-tuning", action="store_true",
-                    help="skip the autotuner (temporal kernel, T = 4, the tiles of FIXED_TILE), e.g. under a profiler")
+                    help="skip the autotuner (the kernels and rows of FIXED_TUNING, T = 4), e.g. under a profiler")
     ap.add_argument("--ref-levels", type=int, default=4, help="time levels per scheme per reference step")
-    ap.add_argument("--profile-case", choices=["k2_tma", "k3_temporal", "kc2_tma"],
+    ap.add_argument("--profile-case", choices=["k2_tma", "k3_temporal", "k5_stream", "kc2_tma"],
                     help="run a short case of one kernel for a profiler capture and exit")
     ap.add_argument("--profile-scheme", type=int, choices=[5, 9, 13], default=13)
     ap.add_argument("--profile-segment", type=int, default=28, help="derived scheme for kc2_tma")

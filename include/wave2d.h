@@ -145,20 +145,33 @@ typedef struct wave2d *wave2d_t;
 
 /* Kernel selection for the two-step.  Zero-initialised = automatic: the
  * one-node kernel below 65536 nodes and for FP64 / FP32x2, the TMA kernel for
- * FP32, and from 2^20 nodes the temporal kernel (T = 4) for the FP32 Section 6
- * schemes on the zero and periodic boundaries. */
+ * FP32, and for the FP32 Section 6 schemes on the zero and periodic
+ * boundaries (without WAVE2D_CANARY) the temporal kernel (T = 4) from 2^20
+ * nodes and the streaming kernel (T = 4) from 2^23 nodes. */
 enum {
     WAVE2D_KERNEL_AUTO = 0,
     WAVE2D_KERNEL_SIMPLE = 1,   /* one thread per node, global loads            */
     WAVE2D_KERNEL_TMA = 2,      /* TMA-staged shared-memory tiles, one step      */
-    WAVE2D_KERNEL_TEMPORAL = 3  /* TMA tiles advanced T steps in shared memory   */
+    WAVE2D_KERNEL_TEMPORAL = 3, /* TMA tiles advanced T steps in shared memory   */
+    WAVE2D_KERNEL_STREAM = 4    /* T steps per launch with the levels in
+                                   registers: one warp walks down a strip of 128
+                                   columns, halo columns by warp shuffles       */
 };
+/* The two multi-level kernels (TEMPORAL, STREAM) take FP32 handles of the
+ * 5-, 9- and 13-point schemes on the zero and periodic boundaries, without
+ * WAVE2D_CANARY; they write out of place (the handle's second pair of level
+ * planes) and finish a run whose length is not a multiple of T with TMA
+ * single steps.  Every kernel evaluates each node identically, so the choice
+ * changes no result bit. */
 
 typedef struct {
     int32_t kernel;       /* WAVE2D_KERNEL_*                                      */
     int32_t tile_h;       /* output rows per tile of WAVE2D_KERNEL_TEMPORAL: 16,
-                             24, 32 or 64; 0 = 32                                 */
-    int32_t temporal_t;   /* steps per launch for WAVE2D_KERNEL_TEMPORAL: 2, 3 or
+                             24, 32 or 64 (0 = 24 for 9 points, else 32); output
+                             rows per strip of WAVE2D_KERNEL_STREAM: 8 .. 4096
+                             (0 = 16 R below 2^25 nodes, else 48; R the stencil
+                             radius)                                              */
+    int32_t temporal_t;   /* steps per launch of the multi-level kernels: 2, 3 or
                              4; 0 = 4                                             */
     int32_t use_graph;    /* capture runs of steps in a CUDA graph: 1 on, 0 off,
                              -1 automatic                                         */
@@ -310,8 +323,9 @@ int wave2d_set_tuning(wave2d_t h, const wave2d_tune *tune);
 
 /* Autotuner: time every candidate two-step configuration for `steps` levels
  * on a copy of the current state (FP32: the TMA one-step kernel at 1 and 2
- * CTAs per SM and the temporal kernel with T in {2, 3, 4} and 16, 24, 32 or 64
- * rows per tile; derived FP32 schemes: the TMA kernel at 1 and 2 CTAs per SM
+ * CTAs per SM, the temporal kernel with T in {2, 3, 4} and 16, 24, 32 or 64
+ * rows per tile, and the streaming kernel with T in {2, 3, 4} and 16, 24, 32
+ * or 48 rows per strip; derived FP32 schemes: the TMA kernel at 1 and 2 CTAs per SM
  * and the one-node kernel; FP64: TMA at 1 and 2 CTAs per SM and the one-node
  * kernel), restore
  * the state exactly (levels, k) and keep the fastest configuration, which is

@@ -1,0 +1,322 @@
+// Register-streaming temporally blocked two-step (Eq. A2 applied T times per
+// HBM round trip, without shared memory).
+//
+// Each warp owns a strip of 128 grid columns (four consecutive nodes per
+// lane) and L output rows, and walks down the strip one input row per step.
+// The step that brings row rho of u^k in computes level t (t = 1..T) on row
+// rho - tR, from the 2R+1 rows of level t-1 around it and row rho - tR of
+// level t-2.  Every level keeps its last 2R+1 rows in registers, in a ring
+// whose slots the unrolled loop addresses statically, so each node is read
+// from HBM once, computed once per level and written once (levels k+T and
+// k+T-1 to the other pair of planes).  Neighbours held by other lanes come by
+// warp shuffles; the lanes at the warp edges compute HX >= R T halo columns
+// that are never written, and the first 2RT rows of a strip only fill the
+// rings (levels whose row is not yet valid are skipped).
+//
+// The per-node arithmetic is that of stencil_ops.cuh (two_step_update and
+// two_step_update_pair with the same operands in the same order), so T levels
+// of this kernel equal T single steps bit for bit.
+//
+// Zero boundary: nodes outside the grid are forced to zero at every level
+// (their inputs come from the ghost ring, which holds zeros).  Periodic
+// boundary: the inputs' ghost ring holds periodic images at least
+// max(HX, R T) nodes deep, and the kernel writes the images of what it stores
+// in the first gw rings.
+#pragma once
+#include <utility>
+
+#include "kernels.cuh"
+
+namespace w2d {
+
+template <int S, int T>
+struct StreamCfg {
+    static constexpr int R = (S == 13) ? 2 : 1;
+    static constexpr int D = R;                         // rows each level trails the one below
+    static constexpr int WIN = 2 * D + 1;               // rows kept per level
+    static constexpr int HX = (R * T + 3) / 4 * 4;      // halo columns per side
+    static constexpr int OW = 128 - 2 * HX;             // output columns per strip
+    static constexpr int HL = HX / 4;                   // halo lanes per side
+    static constexpr int NB = 8;                        // input row slots per warp in shared memory
+    static constexpr int PF = 6;                        // rows copied ahead of the step that uses them
+    static_assert(R * T <= 16 && HX <= 16, "halo must fit the ghost ring");
+    static_assert(PF + 2 <= NB, "a slot is refilled two steps after its last read");
+};
+
+constexpr int kStreamWarps = 4;  // independent warps per CTA
+// shared memory per CTA: every warp's ring of input rows (both planes)
+template <int S, int T>
+constexpr int stream_smem_bytes() {
+    return kStreamWarps * StreamCfg<S, T>::NB * 2 * 32 * 16;
+}
+
+// 16-byte asynchronous copies global -> shared (cp.async, L2 only) and their
+// completion waits.  The waits are hardware waits on this thread's own copies.
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Two 16-byte global stores under one predicate (no branch, so the
+// scheduler can overlap the steps of an unrolled group).
+__device__ __forceinline__ void st2_pred(bool p, float* a, const float (&va)[4], float* b, const float (&vb)[4]) {
+    asm volatile(
+        "{\n .reg .pred q;\n setp.ne.b32 q, %0, 0;\n"
+        " @q st.global.v4.f32 [%1], {%3, %4, %5, %6};\n"
+        " @q st.global.v4.f32 [%2], {%7, %8, %9, %10};\n}" ::"r"((int)p),
+        "l"(a), "l"(b), "f"(va[0]), "f"(va[1]), "f"(va[2]), "f"(va[3]), "f"(vb[0]), "f"(vb[1]), "f"(vb[2]),
+        "f"(vb[3])
+        : "memory");
+}
+
+// Row of a lane in the layout of stencil_ops.cuh: v[k] = column x + k - 2 of
+// the lane's vector at x.  NH columns on each side come from the neighbouring
+// lanes (the lanes at the warp edges receive their own values: halo columns
+// whose results are never stored).
+template <int NH>
+__device__ __forceinline__ void lane_row(const float (&own)[4], float (&v)[8]) {
+    v[2] = own[0];
+    v[3] = own[1];
+    v[4] = own[2];
+    v[5] = own[3];
+    v[0] = v[1] = v[6] = v[7] = 0.0f;
+    if constexpr (NH >= 1) {
+        v[1] = __shfl_up_sync(0xffffffffu, own[3], 1);
+        v[6] = __shfl_down_sync(0xffffffffu, own[0], 1);
+    }
+    if constexpr (NH >= 2) {
+        v[0] = __shfl_up_sync(0xffffffffu, own[2], 1);
+        v[7] = __shfl_down_sync(0xffffffffu, own[1], 1);
+    }
+}
+
+// One level on one row: lv holds level t-1 (own columns) with the row of
+// the updated node in slot CS and row r + d in slot (CS + d) mod WIN; prev is
+// the node's row of level t-2.
+template <int S, int WIN, int CS>
+__device__ __forceinline__ void stream_level(const float (&lv)[WIN][4], const float (&prev)[4], float (&out)[4],
+                                             const Coef3<float>& a, f2x a10x2, f2x a11x2, f2x a20x2) {
+    constexpr int UP = (CS + 1) % WIN, DN = (CS + WIN - 1) % WIN;
+    if constexpr (S == 5) {
+        float c8[8];
+        lane_row<1>(lv[CS], c8);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            Nbr<float> u;
+            u.c = c8[e + 2];
+            u.e = c8[e + 3];
+            u.w = c8[e + 1];
+            u.n = lv[UP][e];
+            u.s = lv[DN][e];
+            out[e] = two_step_update<S>(u, prev[e], a);
+        }
+    } else {
+        constexpr int UP2 = (CS + 2) % WIN, DN2 = (CS + 2 * WIN - 2) % WIN;  // 13-point only
+        float c8[8], up8[8], dn8[8], up28[8], dn28[8];
+        lane_row<(S == 13) ? 2 : 1>(lv[CS], c8);
+        lane_row<1>(lv[UP], up8);
+        lane_row<1>(lv[DN], dn8);
+        lane_row<0>(lv[S == 13 ? UP2 : UP], up28);  // the 9-point pair reads neither
+        lane_row<0>(lv[S == 13 ? DN2 : DN], dn28);
+#pragma unroll
+        for (int e = 0; e < 4; e += 2)
+            two_step_update_pair<S>(c8, up8, dn8, up28, dn28, e, prev[e], prev[e + 1], a10x2, a11x2, a20x2, out[e],
+                                    out[e + 1]);
+    }
+}
+
+template <typename F, int... I>
+__device__ __forceinline__ void static_for_impl(F& f, std::integer_sequence<int, I...>) {
+    (f(std::integral_constant<int, I>{}), ...);
+}
+// f(std::integral_constant<int, i>) for i = 0 .. N-1, unrolled at compile time.
+template <int N, typename F>
+__device__ __forceinline__ void static_for(F&& f) {
+    static_for_impl(f, std::make_integer_sequence<int, N>{});
+}
+
+__device__ __forceinline__ void f4_to(const float4 v, float (&d)[4]) {
+    d[0] = v.x;
+    d[1] = v.y;
+    d[2] = v.z;
+    d[3] = v.w;
+}
+
+// Arguments of one warp's walk down its strip.
+struct StreamWarp {
+    const float* in_cur;
+    const float* in_prev;
+    float* out_cur;
+    float* out_prev;
+    float4* ring;     // this warp's input row slots: slot b, plane p at ring[(2 b + p) * 32]
+    int lane, xl, xload, ymax, rho0, nsteps, gw;
+    bool outlane, edge, vec_images, interior;
+    bool colin[4];
+};
+
+// Copy input step `step` (u^k row rho0 + step, u^{k-1} row rho0 + step - D)
+// into its ring slot and close the copy group.  Rows past the stored band are
+// clamped to its last row (their values reach no stored node).
+template <int D, int NB>
+__device__ __forceinline__ void stream_issue(const StreamWarp& w, const Geo& g, int step) {
+    const int rho = w.rho0 + step;
+    const int b = step % NB;
+    float4* dst = w.ring + 2 * b * 32 + w.lane;
+    cp_async16(smem_u32(dst), w.in_cur + off(g, w.xload, min(rho, w.ymax)));
+    cp_async16(smem_u32(dst + 32), w.in_prev + off(g, w.xload, min(rho - D, w.ymax)));
+    cp_async_commit();
+}
+
+// Stores of output row ro (levels k+T and k+T-1) with every check: partial
+// vectors at the right edge, rows past the grid, periodic images.
+template <bool PER>
+__device__ __forceinline__ void stream_store_checked(const StreamWarp& w, const Geo& g, int ro, const float (&top)[4],
+                                                     const float (&pv)[4]) {
+    if (!w.outlane || ro >= g.ny) return;
+    const size_t o = off(g, w.xl, ro);
+    const int xl = w.xl;
+    if (xl + 4 <= g.nx) {
+        const float4 vc = make_float4(top[0], top[1], top[2], top[3]);
+        const float4 vp = make_float4(pv[0], pv[1], pv[2], pv[3]);
+        *reinterpret_cast<float4*>(w.out_cur + o) = vc;
+        *reinterpret_cast<float4*>(w.out_prev + o) = vp;
+        if (PER && w.edge && w.vec_images) {
+            store_vec_images(reinterpret_cast<float4*>(w.out_cur), g, xl, ro, vc, w.gw, 4);
+            store_vec_images(reinterpret_cast<float4*>(w.out_prev), g, xl, ro, vp, w.gw, 4);
+        }
+    } else {
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+            if (xl + e < g.nx) {
+                w.out_cur[o + e] = top[e];
+                w.out_prev[o + e] = pv[e];
+            }
+    }
+    if (PER && w.edge && !w.vec_images) {
+        const Level Lc{w.out_cur, nullptr}, Lp{w.out_prev, nullptr};
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+            if (xl + e < g.nx) {
+                write_images<DT_F32>(Lc, g, xl + e, ro, top[e], w.gw);
+                write_images<DT_F32>(Lp, g, xl + e, ro, pv[e], w.gw);
+            }
+    }
+}
+
+// WIN consecutive steps from `base` (a multiple of WIN, so ring slots are
+// static).  One body serves every step of every strip, so that the warps of
+// an SM share one instruction stream: levels without valid inputs yet (the
+// first T (D + R) steps) and steps past the end are skipped by warp-uniform
+// branches, and interior strips (full vectors, rows inside the grid, no
+// periodic images) store with predicated instructions.
+template <int S, bool PER, int T>
+__device__ __forceinline__ void stream_group(const StreamWarp& w, const Geo& g, const Coef3<float>& a, f2x a10x2,
+                                             f2x a11x2, f2x a20x2, float (&q)[T][StreamCfg<S, T>::WIN][4],
+                                             int base) {
+    using C = StreamCfg<S, T>;
+    constexpr int R = C::R, D = C::D, WIN = C::WIN, NB = C::NB, PF = C::PF;
+    static_for<WIN>([&](auto sc) {
+        constexpr int s = decltype(sc)::value;
+        const int step = base + s;
+        if (step >= w.nsteps) return;
+        const int rho = w.rho0 + step;
+        cp_async_wait<PF - 1>();  // this step's copy group has landed
+        const float4* src = w.ring + 2 * (step % NB) * 32 + w.lane;
+        f4_to(src[0], q[0][s]);
+        float pm[4];
+        f4_to(src[32], pm);
+        stream_issue<D, NB>(w, g, step + PF);
+        float top[4];  // level T on row rho - T D
+        static_for<T>([&](auto tc) {
+            constexpr int t = decltype(tc)::value + 1;
+            constexpr int cs = ((s - t * D) % WIN + 2 * WIN) % WIN;  // slot of row rho - tD
+            if (step < t * (D + R)) return;  // level t on row rho - tD has no valid inputs yet
+            float out[4];
+            if constexpr (t == 1) stream_level<S, WIN, cs>(q[0], pm, out, a, a10x2, a11x2, a20x2);
+            else stream_level<S, WIN, cs>(q[t - 1], q[t >= 2 ? t - 2 : 0][cs], out, a, a10x2, a11x2, a20x2);
+            if constexpr (!PER) {
+                const int r = rho - t * D;
+                const bool rowin = r >= 0 && r < g.ny;
+#pragma unroll
+                for (int e = 0; e < 4; ++e) out[e] = (rowin && w.colin[e]) ? out[e] : 0.0f;
+            }
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                if constexpr (t < T) q[t < T ? t : 0][cs][e] = out[e];
+                else top[e] = out[e];
+            }
+        });
+        if (step < T * (D + R)) return;  // no output row yet
+        constexpr int ps = ((s - T * D) % WIN + 2 * WIN) % WIN;
+        const float(&pv)[4] = q[T - 1][ps];
+        const int ro = rho - T * D;  // in [y0, y0 + L)
+        if (w.interior) {
+            const size_t o = off(g, w.xl, ro);
+            st2_pred(w.outlane, w.out_cur + o, top, w.out_prev + o, pv);
+        } else {
+            stream_store_checked<PER>(w, g, ro, top, pv);
+        }
+    });
+}
+
+// in_cur / in_prev: planes of u^k and u^{k-1}; out_cur / out_prev: planes
+// that receive u^{k+T} and u^{k+T-1}.  Strip s covers output columns
+// [x0, x0 + OW) with x0 = (s % strips_x) OW and rows [y0, y0 + L) with
+// y0 = (s / strips_x) L.
+template <int S, bool PER, int T>
+__global__ void __launch_bounds__(kStreamWarps * 32)
+    k5_stream(const float* __restrict__ in_cur, const float* __restrict__ in_prev, float* __restrict__ out_cur,
+              float* __restrict__ out_prev, Geo g, Coef3<float> a, int strips_x, int n_strips, int L, int gw) {
+    using C = StreamCfg<S, T>;
+    constexpr int R = C::R, D = C::D, WIN = C::WIN, HX = C::HX, OW = C::OW, NB = C::NB, PF = C::PF;
+    extern __shared__ float4 stream_smem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int strip = blockIdx.x * kStreamWarps + warp;
+    if (strip >= n_strips) return;  // whole warps only; no copies issued yet
+    const int x0 = (strip % strips_x) * OW, y0 = (strip / strips_x) * L;
+    StreamWarp w;
+    w.in_cur = in_cur;
+    w.in_prev = in_prev;
+    w.out_cur = out_cur;
+    w.out_prev = out_prev;
+    w.ring = stream_smem + warp * NB * 2 * 32;
+    w.lane = lane;
+    w.xl = x0 - HX + 4 * lane;                  // grid column of the lane's first node (>= -G)
+    w.xload = min(w.xl, g.pitch - g.G - 4);     // inside the row's storage; clamped lanes are
+                                                // more than R T columns right of the grid
+    w.ymax = g.ny + g.G - 1;                    // last stored row
+    w.rho0 = y0 - R * T;                        // first input row (>= -G)
+    w.nsteps = L + T * (D + R);
+    w.gw = gw;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) w.colin[e] = w.xl + e >= 0 && w.xl + e < g.nx;
+    w.outlane = lane >= C::HL && lane < 32 - C::HL && w.xl < g.nx;
+    w.edge = PER && (x0 < gw || x0 + OW > g.nx - gw || y0 < gw || y0 + L > g.ny - gw);
+    w.vec_images = (g.nx % 4 == 0) && g.nx >= 2 * gw && g.ny >= 2 * gw;
+    w.interior = x0 + OW <= g.nx && y0 + L <= g.ny && !w.edge;
+    const f2x a10x2 = pk2(a.a10, a.a10), a11x2 = pk2(a.a11, a.a11), a20x2 = pk2(a.a20, a.a20);
+
+    // q[t][slot][.]: level t (0 = u^k) at rows whose offset from rho0 is
+    // congruent to slot modulo WIN
+    float q[T][WIN][4];
+#pragma unroll
+    for (int t = 0; t < T; ++t)
+#pragma unroll
+        for (int s = 0; s < WIN; ++s)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) q[t][s][e] = 0.0f;
+#pragma unroll
+    for (int s = 0; s < PF; ++s) stream_issue<D, NB>(w, g, s);
+
+#pragma unroll 1
+    for (int base = 0; base < w.nsteps; base += WIN)
+        stream_group<S, PER, T>(w, g, a, a10x2, a11x2, a20x2, q, base);
+    cp_async_wait_all();  // no copy may land in shared memory after the warp exits
+}
+
+}  // namespace w2d

@@ -1,0 +1,52 @@
+// Launches of the register-streaming temporal kernel (kernels_stream.cuh):
+// one warp per strip of 128 columns and L rows, T two-steps per launch, out
+// of place into the other pair of level planes.
+#include "kernels_stream.cuh"
+#include "wave2d_impl.cuh"
+
+namespace w2d {
+
+template <int S, bool PER, int T>
+static int launch_stream_t(wave2d* h) {
+    using C = StreamCfg<S, T>;
+    auto kern = k5_stream<S, PER, T>;
+    constexpr int smem = stream_smem_bytes<S, T>();
+    const int strips_x = (h->nx + C::OW - 1) / C::OW;
+    const int L = h->temporal_oh;  // rows per strip
+    const int strips_y = (h->ny + L - 1) / L;
+    const int n = strips_x * strips_y;
+    // the levels move to the other pair with their roles kept (plane p -> p ^ 2)
+    const int oc = h->cur ^ 2, op = h->prv ^ 2;
+    const Coef3<float> a{(float)h->a[0], (float)h->a[1], (float)h->a[2]};
+    kern<<<(n + kStreamWarps - 1) / kStreamWarps, kStreamWarps * 32, smem, h->stream>>>(
+        static_cast<const float*>(h->hi[h->cur]), static_cast<const float*>(h->hi[h->prv]),
+        static_cast<float*>(h->hi[oc]), static_cast<float*>(h->hi[op]), h->geo(), a, strips_x, n, L, h->gw);
+    W2D_LAUNCHED("streaming temporal kernel launch");
+    h->cur = oc;
+    h->prv = op;
+    return WAVE2D_OK;
+}
+
+template <int S, bool PER>
+static int launch_stream_sp(wave2d* h) {
+    switch (h->temporal_t) {
+        case 2: return launch_stream_t<S, PER, 2>(h);
+        case 3: return launch_stream_t<S, PER, 3>(h);
+        default: return launch_stream_t<S, PER, 4>(h);
+    }
+}
+
+template <int S>
+static int launch_stream_s(wave2d* h) {
+    return (h->bc == WAVE2D_BC_PERIODIC) ? launch_stream_sp<S, true>(h) : launch_stream_sp<S, false>(h);
+}
+
+int stream_launch(wave2d* h) {
+    switch (h->scheme) {
+        case 5: return launch_stream_s<5>(h);
+        case 9: return launch_stream_s<9>(h);
+        default: return launch_stream_s<13>(h);
+    }
+}
+
+}  // namespace w2d

@@ -166,6 +166,9 @@ static void dispatch_bool(bool v, Fn&& fn) {
     else fn(BC_<false>{});
 }
 
+// Kernels that advance T levels per launch (out of place, full ghost ring).
+static bool is_multilevel(int kernel) { return kernel == WAVE2D_KERNEL_TEMPORAL || kernel == WAVE2D_KERNEL_STREAM; }
+
 // ----------------------------------------------------------- TMA encoding
 static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -456,13 +459,13 @@ static int launch_temporal(wave2d* h) {
 // remain, else one level.  Returns the number of levels advanced (< 0: error).
 static int launch_block(wave2d* h, int64_t remaining) {
     int rc;
-    if (h->kernel == WAVE2D_KERNEL_TEMPORAL && remaining >= h->temporal_t) {
-        rc = launch_temporal(h);
+    if (is_multilevel(h->kernel) && remaining >= h->temporal_t) {
+        rc = (h->kernel == WAVE2D_KERNEL_STREAM) ? stream_launch(h) : launch_temporal(h);
         if (rc != WAVE2D_OK) return rc;
         h->k += h->temporal_t;
         return h->temporal_t;
     }
-    if (h->kernel == WAVE2D_KERNEL_TMA || h->kernel == WAVE2D_KERNEL_TEMPORAL) rc = launch_tma_step(h);
+    if (h->kernel == WAVE2D_KERNEL_TMA || is_multilevel(h->kernel)) rc = launch_tma_step(h);
     else rc = launch_simple_step(h, false);
     if (rc != WAVE2D_OK) return rc;
     std::swap(h->cur, h->prv);
@@ -500,24 +503,36 @@ static void drop_graphs(wave2d* h) {
 static int select_kernel(wave2d* h) {
     int want = h->tune.kernel;
     if (want == WAVE2D_KERNEL_AUTO) {
-        // FP32: TMA tiles once the grid fills the GPU, and from 2^20 nodes the
-        // temporally blocked kernel where it applies (measured faster at
-        // 4096^2 and 8192^2 for every Section 6 scheme).  FP64 and FP32x2 are
-        // bound by arithmetic on GB300 (measured: the one-node kernel is as
-        // fast at 4096^2 and 2.4x faster at 256^2), so they keep it.
+        // FP32: TMA tiles once the grid fills the GPU; where the multi-level
+        // kernels apply, the shared-memory temporal kernel from 2^20 nodes and
+        // the register-streaming kernel from 2^23 (measured on GB300: at
+        // 2048^2 the two tie or the temporal kernel leads, from 4096^2 on the
+        // streaming kernel is faster for every Section 6 scheme).  FP64 and
+        // FP32x2 are bound by arithmetic on GB300 (measured: the one-node
+        // kernel is as fast at 4096^2 and 2.4x faster at 256^2), so they keep it.
         const int64_t nodes = (int64_t)h->nx * h->ny;
         const bool temporal_ok = h->nclass == 0 && h->bc != WAVE2D_BC_ODD && !(h->flags & WAVE2D_CANARY);
         want = (h->dtype != DT_F32 || nodes < 65536) ? WAVE2D_KERNEL_SIMPLE
+               : (temporal_ok && nodes >= (1 << 23)) ? WAVE2D_KERNEL_STREAM
                : (temporal_ok && nodes >= (1 << 20)) ? WAVE2D_KERNEL_TEMPORAL
                                                      : WAVE2D_KERNEL_TMA;
     }
-    if (want == WAVE2D_KERNEL_TEMPORAL &&
+    if (is_multilevel(want) &&
         (h->dtype != DT_F32 || h->nclass > 0 || h->bc == WAVE2D_BC_ODD || (h->flags & WAVE2D_CANARY)))
         want = WAVE2D_KERNEL_TMA;
     if (want == WAVE2D_KERNEL_TMA && h->dtype == DT_F32X2) want = WAVE2D_KERNEL_SIMPLE;
-    if ((want == WAVE2D_KERNEL_TMA || want == WAVE2D_KERNEL_TEMPORAL) && !h->tma_ready) {
-        int rc = prepare_tma(h);
+    if ((want == WAVE2D_KERNEL_TMA || is_multilevel(want)) && !h->tma_ready) {
+        int rc = prepare_tma(h);  // the multi-level kernels finish runs with single TMA steps
         if (rc != WAVE2D_OK) return rc;
+    }
+    if (want == WAVE2D_KERNEL_STREAM) {
+        h->temporal_t = h->tune.temporal_t > 0 ? h->tune.temporal_t : 4;
+        // rows per strip by default: 16 R below 2^25 nodes, else 48 (measured
+        // on GB300 at 4096^2 and 8192^2: the 2RT rows a strip recomputes at
+        // its start cost less than the latency that fewer, longer strips
+        // leave exposed, until the grid holds several waves of strips)
+        const int64_t nodes = (int64_t)h->nx * h->ny;
+        h->temporal_oh = h->tune.tile_h > 0 ? h->tune.tile_h : (nodes < (int64_t(1) << 25) ? 16 * h->R : 48);
     }
     if (want == WAVE2D_KERNEL_TEMPORAL) {
         h->temporal_t = h->tune.temporal_t > 0 ? h->tune.temporal_t : 4;
@@ -529,7 +544,7 @@ static int select_kernel(wave2d* h) {
     }
     // Periodic images: one-level kernels read R nodes beyond an edge, the
     // temporal kernel up to the full ghost ring.
-    const int gw = (want == WAVE2D_KERNEL_TEMPORAL) ? h->G : h->R;
+    const int gw = is_multilevel(want) ? h->G : h->R;
     const bool deeper = gw > h->gw;
     h->gw = gw;
     h->kernel = want;
@@ -860,22 +875,25 @@ void wave2d_destroy(wave2d_t h) { release_handle(h); }
 
 int wave2d_set_tuning(wave2d_t h, const wave2d_tune* tune) {
     if (!h || !tune) return set_error(WAVE2D_ERR_ARG, "null argument");
-    if (tune->kernel < 0 || tune->kernel > WAVE2D_KERNEL_TEMPORAL)
+    if (tune->kernel < 0 || tune->kernel > WAVE2D_KERNEL_STREAM)
         return set_error(WAVE2D_ERR_ARG, "unknown kernel %d", tune->kernel);
     if (tune->kernel == WAVE2D_KERNEL_TMA && h->dtype == WAVE2D_F32X2)
         return set_error(WAVE2D_ERR_ARG, "the TMA kernel supports F32 and F64 storage only");
-    if (tune->kernel == WAVE2D_KERNEL_TEMPORAL && (h->flags & WAVE2D_CANARY))
-        return set_error(WAVE2D_ERR_ARG, "handles with guard-band canaries do not use the temporal kernel");
-    if (tune->kernel == WAVE2D_KERNEL_TEMPORAL && h->bc == WAVE2D_BC_ODD)
-        return set_error(WAVE2D_ERR_ARG, "the temporal kernel covers the zero and periodic boundaries");
-    if (tune->kernel == WAVE2D_KERNEL_TEMPORAL && h->nclass > 0)
+    const bool multi = is_multilevel(tune->kernel);
+    if (multi && (h->flags & WAVE2D_CANARY))
+        return set_error(WAVE2D_ERR_ARG, "handles with guard-band canaries do not use the temporal kernels");
+    if (multi && h->bc == WAVE2D_BC_ODD)
+        return set_error(WAVE2D_ERR_ARG, "the temporal kernels cover the zero and periodic boundaries");
+    if (multi && h->nclass > 0)
         return set_error(WAVE2D_ERR_ARG,
-                         "the temporal kernel covers the 5-, 9- and 13-point schemes with plain sums only");
-    if (tune->kernel == WAVE2D_KERNEL_TEMPORAL && !(tune->temporal_t == 0 || (tune->temporal_t >= 2 && tune->temporal_t <= 4)))
+                         "the temporal kernels cover the 5-, 9- and 13-point schemes with plain sums only");
+    if (multi && !(tune->temporal_t == 0 || (tune->temporal_t >= 2 && tune->temporal_t <= 4)))
         return set_error(WAVE2D_ERR_ARG, "temporal_t must be 0 (auto), 2, 3 or 4 (got %d)", tune->temporal_t);
     if (tune->kernel == WAVE2D_KERNEL_TEMPORAL && !(tune->tile_h == 0 || tune->tile_h == 16 ||
                                                     tune->tile_h == 24 || tune->tile_h == 32 || tune->tile_h == 64))
         return set_error(WAVE2D_ERR_ARG, "temporal tile_h must be 0 (auto), 16, 24, 32 or 64 (got %d)", tune->tile_h);
+    if (tune->kernel == WAVE2D_KERNEL_STREAM && !(tune->tile_h == 0 || (tune->tile_h >= 8 && tune->tile_h <= 4096)))
+        return set_error(WAVE2D_ERR_ARG, "streaming strip rows must be 0 (auto) or 8 .. 4096 (got %d)", tune->tile_h);
     if (tune->ctas_per_sm < 0 || tune->ctas_per_sm > 32)
         return set_error(WAVE2D_ERR_ARG, "ctas_per_sm must be 0 (auto) or 1..32");
     h->tune = *tune;
@@ -905,7 +923,7 @@ int wave2d_get_info(wave2d_t h, wave2d_info_t* info) {
     info->ghost = h->G;
     info->device_bytes = (int64_t)h->base_bytes;
     info->kernel = h->kernel;
-    info->temporal_t = (h->kernel == WAVE2D_KERNEL_TEMPORAL) ? h->temporal_t : 1;
+    info->temporal_t = is_multilevel(h->kernel) ? h->temporal_t : 1;
     info->n_classes = h->nclass;
     info->n_points = h->npoints;
     for (int q = 0; q < 8; ++q) {
@@ -1180,6 +1198,8 @@ int wave2d_autotune(wave2d_t h, int64_t steps, wave2d_tune* best) {
         add(WAVE2D_KERNEL_TMA, 0, 0, 2);
         for (int T : {2, 3, 4})
             for (int oh : {16, 24, 32, 64}) add(WAVE2D_KERNEL_TEMPORAL, oh, T, 0);
+        for (int T : {2, 3, 4})
+            for (int rows : {16, 24, 32, 48}) add(WAVE2D_KERNEL_STREAM, rows, T, 0);
     } else if (h->dtype == WAVE2D_F64) {
         add(WAVE2D_KERNEL_TMA, 0, 0, 1);
         add(WAVE2D_KERNEL_TMA, 0, 0, 2);

@@ -122,6 +122,9 @@ int chain_first_step(wave2d* h, const double* du0, const double* dv0, const Exac
 int chain_simple_step(wave2d* h, bool track, const ExactTab& ex, const Reduce& rd);
 int chain_tma_step(wave2d* h);
 void chain_tma_box(const wave2d* h, int& box_w, int& box_h, int& tile_w, int& tile_h);
+// Register-streaming temporal kernel (stream.cu): T levels of a handle whose
+// kernel is WAVE2D_KERNEL_STREAM, out of place into the other pair of planes.
+int stream_launch(wave2d* h);
 // Guard-band canaries (canary.cu): fill the untouched cells of every plane
 // when the handle has WAVE2D_CANARY.
 int canary_fill(wave2d* h);

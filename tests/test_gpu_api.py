@@ -200,3 +200,21 @@ def test_temporal_tuning_is_validated(w):
         for oh in (16, 24, 32, 64):
             sim.set_tuning(kernel=w.KERNEL_TEMPORAL, temporal_t=2, tile_h=oh)
             assert sim.info().temporal_t == 2
+
+
+def test_stream_tuning_is_validated(w):
+    n = 64
+    with w.Wave2D(n, n, 1.0 / n, 0.5 / n, scheme=9, bc=BC_PERIODIC, dtype=w.F32) as sim:
+        for bad in (dict(temporal_t=1), dict(temporal_t=5), dict(tile_h=7), dict(tile_h=4097), dict(tile_h=-1)):
+            with pytest.raises(w.Wave2DError) as e:
+                sim.set_tuning(kernel=w.KERNEL_STREAM, **bad)
+            assert e.value.code == w.ERR_ARG
+        with pytest.raises(w.Wave2DError) as e:
+            sim.set_tuning(kernel=5)
+        assert e.value.code == w.ERR_ARG
+        for rows in (0, 8, 37, 4096):
+            sim.set_tuning(kernel=w.KERNEL_STREAM, temporal_t=3, tile_h=rows)
+            assert sim.info().kernel == w.KERNEL_STREAM and sim.info().temporal_t == 3
+    with w.Wave2D(n, n, 1.0 / n, 0.5 / n, scheme=9, bc=BC_PERIODIC, dtype=w.F64) as sim:
+        sim.set_tuning(kernel=w.KERNEL_STREAM)   # FP64: falls back to a one-level kernel
+        assert sim.info().kernel in (w.KERNEL_TMA, w.KERNEL_SIMPLE)

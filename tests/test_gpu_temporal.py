@@ -57,6 +57,48 @@ def test_temporal_equals_single_steps_bitwise(w, scheme, bc, T, oh, shape):
     assert np.array_equal(got[1], ref[1]) and np.array_equal(got[0], ref[0])
 
 
+@pytest.mark.parametrize("scheme", [5, 9, 13])
+@pytest.mark.parametrize("bc", [BC_ZERO, BC_PERIODIC], ids=["zero", "periodic"])
+@pytest.mark.parametrize("T,rows", [(2, 32), (3, 64), (4, 0), (4, 8), (4, 37), (4, 64), (4, 256)])
+@pytest.mark.parametrize("shape", SIZES + [(5, 3), (121, 1), (1, 200)], ids=lambda s: f"{s[0]}x{s[1]}")
+def test_stream_equals_single_steps_bitwise(w, scheme, bc, T, rows, shape):
+    """The register-streaming kernel: strips of 128 columns (one warp) and
+    32..256 rows, grids from a single row or column to several strips each
+    way with ragged edges."""
+    nx, ny = shape
+    u0, v0, h = smooth_ic(nx, ny, bc, seed=nx + ny + T + 1)
+    lam = 0.9 * LAMBDA_MAX[scheme]
+    steps = 38
+    ref = run(w, scheme, u0, v0, h, lam, steps, bc, dict(kernel=w.KERNEL_TMA, use_graph=0))
+    got = run(w, scheme, u0, v0, h, lam, steps, bc,
+              dict(kernel=w.KERNEL_STREAM, temporal_t=T, tile_h=rows, use_graph=0))
+    assert np.array_equal(got[1], ref[1]) and np.array_equal(got[0], ref[0])
+
+
+@pytest.mark.parametrize("bc", [BC_ZERO, BC_PERIODIC], ids=["zero", "periodic"])
+def test_stream_mode_switches_graphs_and_oracle(orc, w, bc):
+    n = 260
+    u0, v0, h = smooth_ic(n, n, bc, seed=15)
+    lam = 0.6
+    ref = run(w, 13, u0, v0, h, lam, 150, bc, dict(kernel=w.KERNEL_SIMPLE, use_graph=0))
+    with w.Wave2D(n, n, h, lam * h, scheme=13, bc=bc, dtype=w.F32) as sim:
+        sim.first_step(u0, v0)
+        sim.set_tuning(kernel=w.KERNEL_STREAM, temporal_t=4, tile_h=64, use_graph=1)
+        sim.step_n(70)          # graph replays of 32 levels + 6 more
+        assert sim.info().kernel == w.KERNEL_STREAM and sim.info().temporal_t == 4
+        sim.set_tuning(kernel=w.KERNEL_TEMPORAL, temporal_t=4, use_graph=0)
+        sim.step_n(21)
+        sim.set_tuning(kernel=w.KERNEL_STREAM, temporal_t=3, tile_h=32, use_graph=0)
+        sim.step_n(58)
+        up, uc, k = sim.get_state()
+    assert k == 150
+    assert np.array_equal(uc, ref[1]) and np.array_equal(up, ref[0])
+    rp, rc, _ = orc.run(13, u0, v0, lam, lam * h, 150, bc=bc)
+    for got, want in ((uc, rc), (up, rp)):
+        l2, linf = rel_errors(got, want)
+        assert l2 < TOL[1] and linf < TOL[1], (l2, linf)
+
+
 @pytest.mark.parametrize("scheme", [9, 13])
 @pytest.mark.parametrize("bc", [BC_ZERO, BC_PERIODIC], ids=["zero", "periodic"])
 def test_temporal_parity_with_oracle(orc, w, scheme, bc):
@@ -121,7 +163,7 @@ def test_autotune_restores_state_and_keeps_results(w, dtype):
         after = sim.get_state()
         assert after[2] == before[2] == 11
         assert np.array_equal(after[0], before[0]) and np.array_equal(after[1], before[1])
-        assert best.kernel in (w.KERNEL_TMA, w.KERNEL_TEMPORAL, w.KERNEL_SIMPLE)
+        assert best.kernel in (w.KERNEL_TMA, w.KERNEL_TEMPORAL, w.KERNEL_STREAM, w.KERNEL_SIMPLE)
         sim.step_n(30)
         _, got, _ = sim.get_state()
     with w.Wave2D(n, n, h, 0.6 * h, scheme=13, bc=BC_PERIODIC, dtype=dtype) as ref:
