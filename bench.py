@@ -55,9 +55,9 @@ KNAME = {1: "k2_simple", 2: "k2_tma", 3: "k3_temporal", 4: "k5_stream"}
 # from an ncu capture of the same kernel source (see the profiles directory),
 # keyed by (kernel, hash of the kernel sources, scheme, tile rows) so that a
 # figure is dropped once the kernel or the autotuner's choice changes.
-NCU_TRAFFIC = {("k3_temporal", "5a15dac999df3c2c", 13, 32): 135976448 + 88614656,
-               ("k3_temporal", "5a15dac999df3c2c", 9, 24): 135993600 + 87811584,
-               ("k2_tma", "5a15dac999df3c2c", 13, 0): 135366144 + 19802368}
+NCU_TRAFFIC = {("k5_stream", "c8c89914c5b3aac3", 9, 16): 146468608 + 93931264,
+               ("k5_stream", "c8c89914c5b3aac3", 13, 32): 190684416 + 94103808,
+               ("k2_tma", "c8c89914c5b3aac3", 13, 0): 135371264 + 20168448}
 
 # The autotuner's choice on GB300 (kernel, T = 4, rows per tile or strip),
 # used by --fixed-tuning for profiler runs.
