@@ -50,6 +50,7 @@ FP32_OPS = {5: 9, 9: 14, 13: 19}
 
 # Kernel names by WAVE2D_KERNEL_* value (the profiles use the same names).
 KNAME = {1: "k2_simple", 2: "k2_tma", 3: "k3_temporal", 4: "k5_stream"}
+KSHORT = {1: "simple", 2: "tma", 3: "temporal", 4: "stream"}
 
 # DRAM bytes (read + write) of one launch of a kernel at the benchmark size,
 # from an ncu capture of the same kernel source (see the profiles directory),
@@ -186,6 +187,69 @@ def time_oracle(u0, v0, budget_s: float):
                       f"({pts:.3e} point-updates, {dt:.1f} s)"}
 
 
+def time_oracle_table(u0, v0, budget_s: float = 1.5):
+    """The FP64 oracle, as it stands, on one host thread and on all of them,
+    over bounded samples of the paper's workloads (each sample sized to about
+    budget_s per thread count): the 5-point FP64 256^2 run, the 4096^2
+    benchmark grid (both schemes), periodic plane waves at N <= 1024, the
+    first instances of the batched workload and the first requests of the
+    served stream (each instance run for the same number of levels)."""
+    import numpy as np
+
+    import oracle
+    from initial_data import (BC_PERIODIC, BC_ZERO, LAMBDA_MAX, batch_instances, gaussian_pulse, instance_ic,
+                              plane_wave_ic, plane_wave_k, request_stream)
+    cases = {}
+    g = gaussian_pulse(256, 256, 1.0 / 256, BC_ZERO, sigma=0.05)
+    cases["5point_fp64_256"] = ("5-point, 256^2, lambda 0.5, zero boundary, centred Gaussian",
+                                [(5, g, np.zeros_like(g), 0.5, 0.5 / 256, BC_ZERO)])
+    cases["benchmark_4096"] = ("9- and 13-point, 4096^2 periodic, the benchmark's inputs",
+                               [(s, u0, v0, 0.9 * LAMBDA_MAX[s], 0.9 * LAMBDA_MAX[s] / N, BC_PERIODIC)
+                                for s in SCHEMES])
+    waves = []
+    for n, s, m in ((512, 5, (1, 0)), (1024, 9, (3, 4)), (1024, 13, (32, 16))):
+        k1, k2 = plane_wave_k(n, *m)
+        pu, pv = plane_wave_ic(n, n, 1.0 / n, k1, k2, BC_PERIODIC)
+        lam = 0.9 * LAMBDA_MAX[s]
+        waves.append((s, pu, pv, lam, lam / n, BC_PERIODIC))
+    cases["plane_waves_le_1024"] = ("periodic plane waves: 5-point 512^2 mode (1,0), 9-point 1024^2 mode (3,4), "
+                                    "13-point 1024^2 mode (32,16)", waves)
+
+    def inst_jobs(insts):
+        jobs = []
+        for i in insts:
+            iu, iv, ih = instance_ic(i)
+            jobs.append((i.scheme, iu, iv, i.lam, i.lam * ih, BC_ZERO))
+        return jobs
+    cases["batched_first_16"] = ("the first 16 of the 512 batched instances (seed 4)",
+                                 inst_jobs(batch_instances(512, seed=4)[:16]))
+    cases["served_first_8"] = ("the first 8 of the 2000 served requests (seed 5)",
+                               inst_jobs([r.inst for r in request_stream(2000, seed=5)[:8]]))
+
+    def run_all(jobs, levels):
+        for s, a, b, lam, tau, bc in jobs:
+            oracle.run(s, a, b, lam, tau, levels, bc=bc)
+
+    all_threads = os.cpu_count() or 1
+    out = {}
+    for key, (what, jobs) in cases.items():
+        row = {"sample": what}
+        for threads in (1, all_threads):
+            used = oracle.set_threads(threads)
+            t0 = time.perf_counter()
+            run_all(jobs, 2)
+            probe = time.perf_counter() - t0
+            levels = max(2, int(2 * budget_s / max(probe, 1e-4)))
+            t0 = time.perf_counter()
+            run_all(jobs, levels)
+            dt = time.perf_counter() - t0
+            pts = levels * sum(j[1].size for j in jobs)
+            row[f"threads_{used}"] = {"value": round(pts / dt / 1e9, 5), "levels": levels, "seconds": round(dt, 2)}
+        out[key] = row
+    oracle.set_threads(all_threads)
+    return {"unit": "G point-updates/s", "kind": "oracle", "rows": out}
+
+
 # ----------------------------------------------------------------- GPU arm
 def run_ours(args, rank, world, local_rank):
     import numpy as np
@@ -217,7 +281,7 @@ def run_ours(args, rank, world, local_rank):
             best = w.wave2d_tune(kern, FIXED_TUNING[s][1], 4, -1, 0)
         else:
             best = sims[s].autotune(steps=64)
-        tuned[s] = {"kernel": {1: "simple", 2: "tma", 3: "temporal", 4: "stream"}[best.kernel],
+        tuned[s] = {"kernel": KSHORT[best.kernel],
                     "temporal_t": best.temporal_t, "tile_h": best.tile_h, "ctas_per_sm": best.ctas_per_sm}
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 512 MiB > L2
     torch.cuda.synchronize(dev)
@@ -402,6 +466,8 @@ def run_ours(args, rank, world, local_rank):
         line["fp32_difference_sums"] = measure_diff_sums(w, torch, u0, v0, peak)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = time_oracle(u0, v0, args.cpu_budget)
+        if not args.no_extras:
+            line["oracle_timings"] = time_oracle_table(u0, v0)
     return line
 
 
@@ -546,7 +612,7 @@ def measure_small_fp64(w, torch):
         dt = (time.perf_counter() - t0) / reps
     return {"workload": "5-point, FP64, 256^2, h = 1/256, lambda = 0.5, 200 levels, centred Gaussian, zero boundary",
             "us_per_run": round(dt * 1e6, 1), "value": round(n * n * 200 / dt / 1e9, 3), "unit": "G point-updates/s",
-            "kernel": {1: "simple", 2: "tma", 3: "temporal"}.get(best.kernel), "field_l2": l2,
+            "kernel": KSHORT.get(best.kernel), "field_l2": l2,
             "timing": "host wall clock per run incl. norm to host, 50 runs"}
 
 
@@ -576,7 +642,7 @@ def measure_derived(w, torch, u0, v0, peak):
             sec = e0.elapsed_time(e1) / 1e3 / levels
         out[str(s.n_points)] = {"segment": m, "lambda": round(lam, 6), "us_per_level": round(sec * 1e6, 2),
                                 "value": round(N * N / sec / 1e9, 1), "unit": "G point-updates/s",
-                                "kernel": {1: "simple", 2: "tma", 3: "temporal"}.get(best.kernel),
+                                "kernel": KSHORT.get(best.kernel),
                                 "hbm_frac": round(12 * N * N / sec / 1e9 / peak, 3)}
     return out
 
@@ -610,7 +676,7 @@ def measure_diff_sums(w, torch, u0, v0, peak):
             sec = e0.elapsed_time(e1) / 1e3 / levels
         out[f"{name}_{scheme}"] = {"us_per_level": round(sec * 1e6, 2), "value": round(N * N / sec / 1e9, 1),
                                    "unit": "G point-updates/s",
-                                   "kernel": {1: "simple", 2: "tma", 3: "temporal"}.get(best.kernel),
+                                   "kernel": KSHORT.get(best.kernel),
                                    "bytes_per_node_update": bpn,
                                    "hbm_frac": round(bpn * N * N / sec / 1e9 / peak, 3)}
     return out
