@@ -109,8 +109,9 @@ enum {
                                   more than R rows or R + 4 columns outside the
                                   grid, row padding) with a NaN pattern;
                                   wave2d_canary_check counts cells that changed.
-                                  Such handles do not use the temporal kernel or
-                                  batches (they use the whole ring).             */
+                                  Such handles use the temporal kernels on the
+                                  zero boundary only (periodic images fill the
+                                  whole ring there) and no batches.             */
 };
 
 /* Exact solutions for wave2d_error_vs_exact / wave2d_track_error.
@@ -146,8 +147,8 @@ typedef struct wave2d *wave2d_t;
 /* Kernel selection for the two-step.  Zero-initialised = automatic: the
  * one-node kernel below 65536 nodes and for FP64 / FP32x2, the TMA kernel for
  * FP32, and for the FP32 Section 6 schemes on the zero and periodic
- * boundaries (without WAVE2D_CANARY) the temporal kernel (T = 4) from 2^20
- * nodes and the streaming kernel (T = 4) from 2^23 nodes. */
+ * boundaries (with WAVE2D_CANARY the zero boundary only) the temporal kernel
+ * (T = 4) from 2^20 nodes and the streaming kernel (T = 4) from 2^23 nodes. */
 enum {
     WAVE2D_KERNEL_AUTO = 0,
     WAVE2D_KERNEL_SIMPLE = 1,   /* one thread per node, global loads            */
@@ -158,8 +159,8 @@ enum {
                                    columns, halo columns by warp shuffles       */
 };
 /* The two multi-level kernels (TEMPORAL, STREAM) take FP32 handles of the
- * 5-, 9- and 13-point schemes on the zero and periodic boundaries, without
- * WAVE2D_CANARY; they write out of place (the handle's second pair of level
+ * 5-, 9- and 13-point schemes on the zero and periodic boundaries (with
+ * WAVE2D_CANARY the zero boundary only); they write out of place (the handle's second pair of level
  * planes) and finish a run whose length is not a multiple of T with TMA
  * single steps.  Every kernel evaluates each node identically, so the choice
  * changes no result bit. */

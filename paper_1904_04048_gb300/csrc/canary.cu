@@ -2,9 +2,11 @@
 // kernels write (R rings of images; in x up to three more columns, where a
 // periodic image is stored as a whole 16-byte vector), every level plane
 // holds cells that no kernel of such a handle may write and whose values no
-// result depends on: the rest of the ghost ring and the row padding.  They
-// are filled with a NaN bit pattern; wave2d_canary_check counts cells whose
-// bits changed, a check against stray writes into the planes.
+// result depends on: the rest of the ghost ring and the row padding.  (The
+// temporal kernels of a zero-boundary handle read them, for nodes outside the
+// grid that they force to zero, and write none.)  They are filled with a NaN
+// bit pattern; wave2d_canary_check counts cells whose bits changed, a check
+// against stray writes into the planes.
 #include "wave2d_impl.cuh"
 
 namespace w2d {

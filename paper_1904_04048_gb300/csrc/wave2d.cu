@@ -168,6 +168,13 @@ static void dispatch_bool(bool v, Fn&& fn) {
 
 // Kernels that advance T levels per launch (out of place, full ghost ring).
 static bool is_multilevel(int kernel) { return kernel == WAVE2D_KERNEL_TEMPORAL || kernel == WAVE2D_KERNEL_STREAM; }
+// Handles those kernels take (FP32 is checked separately): the Section 6
+// schemes with plain sums, zero or periodic boundary; with guard-band
+// canaries the zero boundary only, where they write inside the grid alone
+// (the ghost cells they read beyond R feed only nodes forced to zero).
+static bool multilevel_ok(const wave2d* h) {
+    return h->nclass == 0 && h->bc != WAVE2D_BC_ODD && !((h->flags & WAVE2D_CANARY) && h->bc != WAVE2D_BC_ZERO);
+}
 
 // ----------------------------------------------------------- TMA encoding
 static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
@@ -511,15 +518,13 @@ static int select_kernel(wave2d* h) {
         // FP32x2 are bound by arithmetic on GB300 (measured: the one-node
         // kernel is as fast at 4096^2 and 2.4x faster at 256^2), so they keep it.
         const int64_t nodes = (int64_t)h->nx * h->ny;
-        const bool temporal_ok = h->nclass == 0 && h->bc != WAVE2D_BC_ODD && !(h->flags & WAVE2D_CANARY);
+        const bool temporal_ok = multilevel_ok(h);
         want = (h->dtype != DT_F32 || nodes < 65536) ? WAVE2D_KERNEL_SIMPLE
                : (temporal_ok && nodes >= (1 << 23)) ? WAVE2D_KERNEL_STREAM
                : (temporal_ok && nodes >= (1 << 20)) ? WAVE2D_KERNEL_TEMPORAL
                                                      : WAVE2D_KERNEL_TMA;
     }
-    if (is_multilevel(want) &&
-        (h->dtype != DT_F32 || h->nclass > 0 || h->bc == WAVE2D_BC_ODD || (h->flags & WAVE2D_CANARY)))
-        want = WAVE2D_KERNEL_TMA;
+    if (is_multilevel(want) && (h->dtype != DT_F32 || !multilevel_ok(h))) want = WAVE2D_KERNEL_TMA;
     if (want == WAVE2D_KERNEL_TMA && h->dtype == DT_F32X2) want = WAVE2D_KERNEL_SIMPLE;
     if ((want == WAVE2D_KERNEL_TMA || is_multilevel(want)) && !h->tma_ready) {
         int rc = prepare_tma(h);  // the multi-level kernels finish runs with single TMA steps
@@ -880,8 +885,10 @@ int wave2d_set_tuning(wave2d_t h, const wave2d_tune* tune) {
     if (tune->kernel == WAVE2D_KERNEL_TMA && h->dtype == WAVE2D_F32X2)
         return set_error(WAVE2D_ERR_ARG, "the TMA kernel supports F32 and F64 storage only");
     const bool multi = is_multilevel(tune->kernel);
-    if (multi && (h->flags & WAVE2D_CANARY))
-        return set_error(WAVE2D_ERR_ARG, "handles with guard-band canaries do not use the temporal kernels");
+    if (multi && (h->flags & WAVE2D_CANARY) && h->bc != WAVE2D_BC_ZERO)
+        return set_error(WAVE2D_ERR_ARG,
+                         "with guard-band canaries the temporal kernels take the zero boundary only (periodic "
+                         "images fill the whole ghost ring)");
     if (multi && h->bc == WAVE2D_BC_ODD)
         return set_error(WAVE2D_ERR_ARG, "the temporal kernels cover the zero and periodic boundaries");
     if (multi && h->nclass > 0)
@@ -1189,7 +1196,7 @@ int wave2d_autotune(wave2d_t h, int64_t steps, wave2d_tune* best) {
         t.ctas_per_sm = per_sm;
         cands.push_back(t);
     };
-    if (h->dtype == WAVE2D_F32 && (h->nclass > 0 || h->bc == WAVE2D_BC_ODD || (h->flags & WAVE2D_CANARY))) {
+    if (h->dtype == WAVE2D_F32 && !multilevel_ok(h)) {
         add(WAVE2D_KERNEL_TMA, 0, 0, 1);
         add(WAVE2D_KERNEL_TMA, 0, 0, 2);
         add(WAVE2D_KERNEL_SIMPLE, 0, 0, 0);

@@ -1,9 +1,10 @@
 """Guard-band canaries (WAVE2D_CANARY) as a stand-in for a memory checker:
 every kernel path of the one-level stepping (all schemes, storage types,
 boundaries, kernels, difference sums and form), with state loads, raw
-checkpoints, norms, error tracking and the autotuner, must leave the NaN
-pattern in the untouched part of every plane intact; results stay equal to
-those of a handle without canaries."""
+checkpoints, norms, error tracking and the autotuner, and the two temporal
+kernels on the zero boundary, must leave the NaN pattern in the untouched
+part of every plane intact; results stay equal to those of a handle without
+canaries."""
 import numpy as np
 import pytest
 
@@ -80,15 +81,45 @@ def test_derived_paths_keep_the_guard_band(w, m, dtype, bc, kernel):
     _exercise(w, w.derive_scheme(m), dtype, bc, kernel, 0, (150, 41))
 
 
+@pytest.mark.parametrize("scheme", [5, 9, 13])
+@pytest.mark.parametrize("kernel,T,rows", [(3, 4, 16), (3, 2, 32), (4, 4, 8), (4, 3, 37), (4, 4, 0)],
+                         ids=["temporal-4-16", "temporal-2-32", "stream-4-8", "stream-3-37", "stream-4-auto"])
+@pytest.mark.parametrize("shape", [(13, 31), (130, 70), (300, 97)], ids=lambda s: f"{s[0]}x{s[1]}")
+def test_multilevel_kernels_keep_the_guard_band(w, scheme, kernel, T, rows, shape):
+    """Zero boundary: the temporal kernels read ghost cells up to R T rows and
+    16 columns out (canaries included, for nodes they force to zero) and must
+    write inside the grid only; results equal a handle without canaries."""
+    nx, ny = shape
+    u0, v0, h = smooth_ic(nx, ny, BC_ZERO, seed=nx + T)
+    lam = 0.5
+    out = []
+    for extra in (w.CANARY, 0):
+        with w.Wave2D(nx, ny, h, lam * h, scheme=scheme, bc=BC_ZERO, dtype=w.F32, flags=extra) as sim:
+            sim.set_tuning(kernel=kernel, temporal_t=T, tile_h=rows, use_graph=0)
+            sim.first_step(u0, v0)
+            sim.step_n(21)                                # T-level launches and single steps
+            raw, k = sim.get_raw()
+            sim.set_raw(raw, k)
+            sim.set_tuning(kernel=kernel, temporal_t=T, tile_h=rows, use_graph=1)
+            sim.step_n(40)                                # graph replays
+            if extra:
+                assert sim.canary_check() == 0
+            out.append(sim.get_state())
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+
+
 def test_canary_refusals(w):
     n = 64
     with w.Wave2D(n, n, 1.0 / n, 0.5 / n, scheme=13, dtype=w.F32, flags=w.CANARY) as sim:
-        with pytest.raises(w.Wave2DError) as e:
-            sim.set_tuning(kernel=w.KERNEL_TEMPORAL)
-        assert e.value.code == w.ERR_ARG
+        sim.set_tuning(kernel=w.KERNEL_STREAM)           # zero boundary: allowed
         with pytest.raises(w.Wave2DError) as e:
             w.Batch([sim])
         assert e.value.code == w.ERR_ARG
+    with w.Wave2D(n, n, 1.0 / n, 0.5 / n, scheme=13, bc=BC_PERIODIC, dtype=w.F32, flags=w.CANARY) as sim:
+        for kernel in (w.KERNEL_TEMPORAL, w.KERNEL_STREAM):
+            with pytest.raises(w.Wave2DError) as e:
+                sim.set_tuning(kernel=kernel)
+            assert e.value.code == w.ERR_ARG
     with w.Wave2D(n, n, 1.0 / n, 0.5 / n, scheme=13, dtype=w.F32) as sim:
         with pytest.raises(w.Wave2DError) as e:
             sim.canary_check()
