@@ -1,0 +1,92 @@
+"""Index arithmetic of the register-streaming kernel (k5_stream), replayed on
+the CPU: for ragged and degenerate grids, every strip height the tuning
+accepts near the edges and every scheme and depth, each global load stays in
+the level plane (ghost ring and row padding included) at a 16-byte aligned
+address, the cp.async ring slots stay in the CTA's shared memory, and the
+stored vectors cover every grid node exactly once.
+
+The model restates the kernel's constants and formulas (kernels_stream.cuh):
+strips of 32 C columns (C = 4 nodes per lane) with HX = R T rounded up to a
+vector of halo columns on each side, L output rows, input rows
+rho0 = y0 - R T .. rho0 + L + 2 R T - 1 plus the PF rows copied ahead,
+u^{k-1} rows one stencil radius behind, rows clamped to the last stored row,
+columns to the last 4-node vector of the stored row."""
+import itertools
+
+import pytest
+
+G = 16            # ghost ring width (kGhost)
+C = 4             # nodes per lane
+NB, PF = 8, 6     # ring slots per warp, rows copied ahead
+WARPS = 4         # warps per CTA
+
+
+def plane_geometry(nx, ny):
+    pitch = -(-(nx + 2 * G) // 32) * 32
+    return pitch, ny + 2 * G
+
+
+def replay(nx, ny, scheme, T, L):
+    R = 2 if scheme == 13 else 1
+    HX = (R * T + 3) // 4 * 4
+    W = 32 * C
+    OW = W - 2 * HX
+    pitch, rows = plane_geometry(nx, ny)
+    n_el = pitch * rows
+    strips_x, strips_y = -(-nx // OW), -(-ny // L)
+    ymax = ny + G - 1
+
+    def off(i, j):
+        return (j + G) * pitch + (i + G)
+
+    covered = {}
+    for strip in range(strips_x * strips_y):
+        warp = strip % WARPS
+        x0, y0 = (strip % strips_x) * OW, (strip // strips_x) * L
+        rho0, nsteps = y0 - R * T, L + 2 * R * T
+        for lane in range(32):
+            xl = x0 - HX + C * lane
+            xload = min(xl, pitch - G - C)
+            assert xl >= -G
+            for step in range(nsteps + PF):            # copies issued up to PF steps ahead
+                rho = rho0 + step
+                for y in (rho, rho - R):                # u^k row and u^{k-1} row
+                    o = off(xload, min(y, ymax))
+                    assert 0 <= o and o + C <= n_el and o % 4 == 0
+                slot = step % NB
+                smem = ((warp * NB + slot) * 2 + 1) * 32 + lane   # plane 1 is the larger index
+                assert smem < WARPS * NB * 2 * 32
+            if not (HX <= C * lane < HX + OW and xl < nx):
+                continue
+            for step in range(2 * R * T, nsteps):
+                ro = rho0 + step - T * R
+                assert y0 <= ro < y0 + L
+                if ro >= ny:
+                    continue
+                for e in range(4):
+                    if xl + e < nx:
+                        o = off(xl + e, ro)
+                        assert 0 <= o < n_el
+                        covered[(xl + e, ro)] = covered.get((xl + e, ro), 0) + 1
+    assert len(covered) == nx * ny and set(covered.values()) == {1}
+
+
+SHAPES = [(1, 1), (5, 3), (13, 31), (64, 64), (121, 1), (1, 200), (120, 17), (300, 97), (1000, 333)]
+
+
+@pytest.mark.parametrize("scheme", [5, 9, 13])
+@pytest.mark.parametrize("T", [2, 3, 4])
+@pytest.mark.parametrize("L", [8, 16, 37, 64])
+def test_loads_in_bounds_and_stores_cover_each_node_once(scheme, T, L):
+    for nx, ny in SHAPES:
+        replay(nx, ny, scheme, T, L)
+
+
+def test_halo_reaches_every_dependency():
+    """A node stored at level T depends on level-0 nodes up to R T rows and
+    columns away; the strip's halo columns and warm-up rows must hold all of
+    them (else a stored node would read a halo lane's unfinished value)."""
+    for scheme, T in itertools.product((5, 9, 13), (2, 3, 4)):
+        R = 2 if scheme == 13 else 1
+        HX = (R * T + 3) // 4 * 4
+        assert HX >= R * T and HX <= G and R * (T + 1) <= G
