@@ -20,8 +20,11 @@
 // Zero boundary: nodes outside the grid are forced to zero at every level
 // (their inputs come from the ghost ring, which holds zeros).  Periodic
 // boundary: the inputs' ghost ring holds periodic images at least
-// max(HX, R T) nodes deep, and the kernel writes the images of what it stores
-// in the first gw rings.
+// max(HX, R T) nodes deep.  The kernel stores grid nodes only, and
+// k5_ring_images copies the images of both output levels into the first gw
+// rings afterwards (measured on GB300 at 4096^2: image stores inside the
+// kernel made the 13-point level 23.0 us instead of 19.5 with the copy; the
+// 9-point level is the same either way).
 #pragma once
 #include <utility>
 
@@ -154,8 +157,8 @@ struct StreamWarp {
     float* out_cur;
     float* out_prev;
     float4* ring;     // this warp's input row slots: slot b, plane p at ring[(2 b + p) * 32]
-    int lane, xl, xload, ymax, rho0, nsteps, gw;
-    bool outlane, edge, vec_images, interior;
+    int lane, xl, xload, ymax, rho0, nsteps;
+    bool outlane, interior;
     bool colin[4];
 };
 
@@ -173,22 +176,15 @@ __device__ __forceinline__ void stream_issue(const StreamWarp& w, const Geo& g, 
 }
 
 // Stores of output row ro (levels k+T and k+T-1) with every check: partial
-// vectors at the right edge, rows past the grid, periodic images.
-template <bool PER>
+// vectors at the right edge, rows past the grid.
 __device__ __forceinline__ void stream_store_checked(const StreamWarp& w, const Geo& g, int ro, const float (&top)[4],
                                                      const float (&pv)[4]) {
     if (!w.outlane || ro >= g.ny) return;
     const size_t o = off(g, w.xl, ro);
     const int xl = w.xl;
     if (xl + 4 <= g.nx) {
-        const float4 vc = make_float4(top[0], top[1], top[2], top[3]);
-        const float4 vp = make_float4(pv[0], pv[1], pv[2], pv[3]);
-        *reinterpret_cast<float4*>(w.out_cur + o) = vc;
-        *reinterpret_cast<float4*>(w.out_prev + o) = vp;
-        if (PER && w.edge && w.vec_images) {
-            store_vec_images(reinterpret_cast<float4*>(w.out_cur), g, xl, ro, vc, w.gw, 4);
-            store_vec_images(reinterpret_cast<float4*>(w.out_prev), g, xl, ro, vp, w.gw, 4);
-        }
+        *reinterpret_cast<float4*>(w.out_cur + o) = make_float4(top[0], top[1], top[2], top[3]);
+        *reinterpret_cast<float4*>(w.out_prev + o) = make_float4(pv[0], pv[1], pv[2], pv[3]);
     } else {
 #pragma unroll
         for (int e = 0; e < 4; ++e)
@@ -197,23 +193,14 @@ __device__ __forceinline__ void stream_store_checked(const StreamWarp& w, const 
                 w.out_prev[o + e] = pv[e];
             }
     }
-    if (PER && w.edge && !w.vec_images) {
-        const Level Lc{w.out_cur, nullptr}, Lp{w.out_prev, nullptr};
-#pragma unroll
-        for (int e = 0; e < 4; ++e)
-            if (xl + e < g.nx) {
-                write_images<DT_F32>(Lc, g, xl + e, ro, top[e], w.gw);
-                write_images<DT_F32>(Lp, g, xl + e, ro, pv[e], w.gw);
-            }
-    }
 }
 
 // WIN consecutive steps from `base` (a multiple of WIN, so ring slots are
 // static).  One body serves every step of every strip, so that the warps of
 // an SM share one instruction stream: levels without valid inputs yet (the
 // first T (D + R) steps) and steps past the end are skipped by warp-uniform
-// branches, and interior strips (full vectors, rows inside the grid, no
-// periodic images) store with predicated instructions.
+// branches, and interior strips (full vectors, rows inside the grid) store
+// with predicated instructions.
 template <int S, bool PER, int T>
 __device__ __forceinline__ void stream_group(const StreamWarp& w, const Geo& g, const Coef3<float>& a, f2x a10x2,
                                              f2x a11x2, f2x a20x2, float (&q)[T][StreamCfg<S, T>::WIN][4],
@@ -259,7 +246,7 @@ __device__ __forceinline__ void stream_group(const StreamWarp& w, const Geo& g, 
             const size_t o = off(g, w.xl, ro);
             st2_pred(w.outlane, w.out_cur + o, top, w.out_prev + o, pv);
         } else {
-            stream_store_checked<PER>(w, g, ro, top, pv);
+            stream_store_checked(w, g, ro, top, pv);
         }
     });
 }
@@ -271,7 +258,7 @@ __device__ __forceinline__ void stream_group(const StreamWarp& w, const Geo& g, 
 template <int S, bool PER, int T>
 __global__ void __launch_bounds__(kStreamWarps * 32)
     k5_stream(const float* __restrict__ in_cur, const float* __restrict__ in_prev, float* __restrict__ out_cur,
-              float* __restrict__ out_prev, Geo g, Coef3<float> a, int strips_x, int n_strips, int L, int gw) {
+              float* __restrict__ out_prev, Geo g, Coef3<float> a, int strips_x, int n_strips, int L) {
     using C = StreamCfg<S, T>;
     constexpr int R = C::R, D = C::D, WIN = C::WIN, HX = C::HX, OW = C::OW, NB = C::NB, PF = C::PF;
     extern __shared__ float4 stream_smem[];
@@ -292,13 +279,10 @@ __global__ void __launch_bounds__(kStreamWarps * 32)
     w.ymax = g.ny + g.G - 1;                    // last stored row
     w.rho0 = y0 - R * T;                        // first input row (>= -G)
     w.nsteps = L + T * (D + R);
-    w.gw = gw;
 #pragma unroll
     for (int e = 0; e < 4; ++e) w.colin[e] = w.xl + e >= 0 && w.xl + e < g.nx;
     w.outlane = lane >= C::HL && lane < 32 - C::HL && w.xl < g.nx;
-    w.edge = PER && (x0 < gw || x0 + OW > g.nx - gw || y0 < gw || y0 + L > g.ny - gw);
-    w.vec_images = (g.nx % 4 == 0) && g.nx >= 2 * gw && g.ny >= 2 * gw;
-    w.interior = x0 + OW <= g.nx && y0 + L <= g.ny && !w.edge;
+    w.interior = x0 + OW <= g.nx && y0 + L <= g.ny;
     const f2x a10x2 = pk2(a.a10, a.a10), a11x2 = pk2(a.a11, a.a11), a20x2 = pk2(a.a20, a.a20);
 
     // q[t][slot][.]: level t (0 = u^k) at rows whose offset from rho0 is
@@ -317,6 +301,39 @@ __global__ void __launch_bounds__(kStreamWarps * 32)
     for (int base = 0; base < w.nsteps; base += WIN)
         stream_group<S, PER, T>(w, g, a, a10x2, a11x2, a20x2, q, base);
     cp_async_wait_all();  // no copy may land in shared memory after the warp exits
+}
+
+// Periodic images of the two levels a streaming launch wrote, in the first gw
+// rings, each ring cell copying the grid node it images.  Blocks with
+// blockIdx.y < 2 gw copy one row of the top (y < gw) or bottom band over the
+// ring's full width; the others copy the left and right bands, eight grid
+// rows per 256 threads (2 gw = 32 cells per row).  blockIdx.z is the plane.
+__device__ __forceinline__ int wrap_index(int i, int n) {
+    if (i >= 0 && i < n) return i;
+    if (i < 0 && i + n >= 0) return i + n;
+    if (i >= n && i - n < n) return i - n;
+    return ((i % n) + n) % n;  // grids narrower than the ring
+}
+
+__global__ void __launch_bounds__(256) k5_ring_images(float* __restrict__ a, float* __restrict__ b, Geo g, int gw) {
+    float* p = blockIdx.z ? b : a;
+    const int t = threadIdx.x;
+    if ((int)blockIdx.y < 2 * gw) {
+        const int r = blockIdx.y;
+        const int j = r < gw ? r - gw : g.ny + (r - gw);
+        const int sj = wrap_index(j, g.ny);
+        for (int i = (int)blockIdx.x * 256 + t - gw; i < g.nx + gw; i += gridDim.x * 256)
+            p[off(g, i, j)] = p[off(g, wrap_index(i, g.nx), sj)];
+    } else {
+        const int rows_per_block = max(1, 256 / (2 * gw));  // gw <= 16 in every handle
+        for (int base = ((int)blockIdx.y - 2 * gw) * gridDim.x + blockIdx.x; base * rows_per_block < g.ny;
+             base += (gridDim.y - 2 * gw) * gridDim.x) {
+            const int j = base * rows_per_block + t / (2 * gw), c = t % (2 * gw);
+            if (j >= g.ny || t >= rows_per_block * 2 * gw) continue;
+            const int i = c < gw ? c - gw : g.nx + (c - gw);
+            p[off(g, i, j)] = p[off(g, wrap_index(i, g.nx), j)];
+        }
+    }
 }
 
 }  // namespace w2d

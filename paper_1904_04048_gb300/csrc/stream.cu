@@ -1,6 +1,8 @@
 // Launches of the register-streaming temporal kernel (kernels_stream.cuh):
 // one warp per strip of 128 columns and L rows, T two-steps per launch, out
 // of place into the other pair of level planes.
+#include <algorithm>
+
 #include "kernels_stream.cuh"
 #include "wave2d_impl.cuh"
 
@@ -20,8 +22,16 @@ static int launch_stream_t(wave2d* h) {
     const Coef3<float> a{(float)h->a[0], (float)h->a[1], (float)h->a[2]};
     kern<<<(n + kStreamWarps - 1) / kStreamWarps, kStreamWarps * 32, smem, h->stream>>>(
         static_cast<const float*>(h->hi[h->cur]), static_cast<const float*>(h->hi[h->prv]),
-        static_cast<float*>(h->hi[oc]), static_cast<float*>(h->hi[op]), h->geo(), a, strips_x, n, L, h->gw);
+        static_cast<float*>(h->hi[oc]), static_cast<float*>(h->hi[op]), h->geo(), a, strips_x, n, L);
     W2D_LAUNCHED("streaming temporal kernel launch");
+    if constexpr (PER) {  // periodic images of both output levels in the first gw rings
+        // grid: x spans a band row, y = 2 gw band rows + the side-band blocks
+        const int gx = std::min((h->nx + 2 * h->gw + 255) / 256, 16);
+        const int side = std::max(1, std::min((h->ny * 2 * h->gw + 255) / 256 / gx, 64));
+        k5_ring_images<<<dim3(gx, 2 * h->gw + side, 2), 256, 0, h->stream>>>(
+            static_cast<float*>(h->hi[oc]), static_cast<float*>(h->hi[op]), h->geo(), h->gw);
+        W2D_LAUNCHED("periodic image kernel launch");
+    }
     h->cur = oc;
     h->prv = op;
     return WAVE2D_OK;

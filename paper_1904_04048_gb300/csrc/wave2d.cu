@@ -1029,7 +1029,11 @@ int wave2d_error_vs_exact(wave2d_t h, const wave2d_exact* ex, double* rel_l2, do
     }
     const ExactTab et = make_tab(h, h->tab_eval, *ex, (double)h->k * h->tau);
     const Reduce rd = make_reduce(h, h->acc_eval, 0);
-    const dim3 grd(std::min((h->nx + 255) / 256, 64), std::min(h->ny, 1024));
+    // about 8 blocks per SM, each thread looping over many nodes: every block
+    // ends in a block reduction and one atomic on the shared counter, which
+    // dominated the time at 4096^2 with a block per row
+    const int gx = std::min((h->nx + 255) / 256, 16);
+    const dim3 grd(gx, std::max(1, std::min(h->ny, 8 * h->num_sms / gx)));
     dispatch_dt(h->dtype, [&](auto DTc) {
         k4_norms<decltype(DTc)::value><<<grd, 256, 0, h->stream>>>(h->level(h->cur), h->geo(), et, rd);
     });

@@ -90,3 +90,47 @@ def test_halo_reaches_every_dependency():
         R = 2 if scheme == 13 else 1
         HX = (R * T + 3) // 4 * 4
         assert HX >= R * T and HX <= G and R * (T + 1) <= G
+
+
+def wrap(i, n):
+    return i % n
+
+
+def ring_cells(nx, ny, gw):
+    """The (cell, source) pairs k5_ring_images writes for one plane, with the
+    launch's grid (x blocks over a band row, y = 2 gw band rows plus the
+    side-band blocks) and its loops replayed thread by thread."""
+    gx = min((nx + 2 * gw + 255) // 256, 16)
+    side = max(1, min((ny * 2 * gw + 255) // 256 // gx, 64))
+    out = []
+    for by in range(2 * gw + side):
+        for bx in range(gx):
+            for t in range(256):
+                if by < 2 * gw:
+                    j = by - gw if by < gw else ny + (by - gw)
+                    i = bx * 256 + t - gw
+                    while i < nx + gw:
+                        out.append(((i, j), (wrap(i, nx), wrap(j, ny))))
+                        i += gx * 256
+                else:
+                    rpb = max(1, 256 // (2 * gw))
+                    base = (by - 2 * gw) * gx + bx
+                    while base * rpb < ny:
+                        j, c = base * rpb + t // (2 * gw), t % (2 * gw)
+                        if j < ny and t < rpb * 2 * gw:
+                            i = c - gw if c < gw else nx + (c - gw)
+                            out.append(((i, j), (wrap(i, nx), j)))
+                        base += side * gx
+    return out
+
+
+@pytest.mark.parametrize("nx,ny", [(1, 1), (5, 3), (13, 31), (120, 17), (300, 97), (700, 2)])
+def test_ring_images_cover_the_ring_once(nx, ny):
+    gw = G
+    cells = ring_cells(nx, ny, gw)
+    targets = [c for c, _ in cells]
+    ring = {(i, j) for i in range(-gw, nx + gw) for j in range(-gw, ny + gw)
+            if not (0 <= i < nx and 0 <= j < ny)}
+    assert len(targets) == len(set(targets)) and set(targets) == ring
+    for (i, j), (si, sj) in cells:
+        assert 0 <= si < nx and 0 <= sj < ny and (si - i) % nx == 0 and (sj - j) % ny == 0
