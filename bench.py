@@ -62,7 +62,7 @@ NCU_TRAFFIC = {("k5_stream", "c8c89914c5b3aac3", 9, 16): 146468608 + 93931264,
 
 # The autotuner's choice on GB300 (kernel, T = 4, rows per tile or strip),
 # used by --fixed-tuning for profiler runs.
-FIXED_TUNING = {9: ("stream", 16), 13: ("stream", 32)}
+FIXED_TUNING = {9: ("stream", 48), 13: ("stream", 32)}
 
 
 def kernel_source_hash() -> str:

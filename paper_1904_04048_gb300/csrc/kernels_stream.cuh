@@ -19,12 +19,16 @@
 //
 // Zero boundary: nodes outside the grid are forced to zero at every level
 // (their inputs come from the ghost ring, which holds zeros).  Periodic
-// boundary: the inputs' ghost ring holds periodic images at least
-// max(HX, R T) nodes deep.  The kernel stores grid nodes only, and
-// k5_ring_images copies the images of both output levels into the first gw
-// rings afterwards (measured on GB300 at 4096^2: image stores inside the
-// kernel made the 13-point level 23.0 us instead of 19.5 with the copy; the
-// 9-point level is the same either way).
+// boundary: the kernel stores grid nodes only.  When nx is a multiple of 4 it
+// reads its inputs at wrapped coordinates (a lane's 4-node vector wraps as a
+// whole; rows wrap per step), so the ghost ring is neither read nor kept up
+// to date between launches, and k5_ring_images rebuilds the images once,
+// before a kernel that reads the ring runs (the caller tracks this).
+// Otherwise the inputs' ghost ring holds periodic images at least R (T + 1)
+// rows and HX columns deep and k5_ring_images copies them after every launch.
+// (Measured on GB300 at 4096^2: image stores inside the kernel made the
+// 13-point level 23.0 us instead of 19.5 with a copy per launch; the copy
+// itself was 7 % of the device time.)
 #pragma once
 #include <utility>
 
@@ -157,7 +161,8 @@ struct StreamWarp {
     float* out_cur;
     float* out_prev;
     float4* ring;     // this warp's input row slots: slot b, plane p at ring[(2 b + p) * 32]
-    int lane, xl, xload, ymax, rho0, nsteps;
+    int lane, xl, xload, ymax, rho0, nsteps, ny;
+    bool wrap;  // periodic inputs read at wrapped coordinates (the ghost ring is not read)
     bool outlane, interior;
     bool colin[4];
 };
@@ -165,13 +170,21 @@ struct StreamWarp {
 // Copy input step `step` (u^k row rho0 + step, u^{k-1} row rho0 + step - D)
 // into its ring slot and close the copy group.  Rows past the stored band are
 // clamped to its last row (their values reach no stored node).
+// Stored row of input row y: clamped to the stored band, or wrapped.
+__device__ __forceinline__ int stream_row(const StreamWarp& w, int y) {
+    if (!w.wrap) return min(y, w.ymax);
+    if (y < 0) return y + w.ny;  // y >= -R (T + 1) > -ny (ny >= 16 when wrapping)
+    if (y < w.ny) return y;
+    return y - w.ny < w.ny ? y - w.ny : y % w.ny;
+}
+
 template <int D, int NB>
 __device__ __forceinline__ void stream_issue(const StreamWarp& w, const Geo& g, int step) {
     const int rho = w.rho0 + step;
     const int b = step % NB;
     float4* dst = w.ring + 2 * b * 32 + w.lane;
-    cp_async16(smem_u32(dst), w.in_cur + off(g, w.xload, min(rho, w.ymax)));
-    cp_async16(smem_u32(dst + 32), w.in_prev + off(g, w.xload, min(rho - D, w.ymax)));
+    cp_async16(smem_u32(dst), w.in_cur + off(g, w.xload, stream_row(w, rho)));
+    cp_async16(smem_u32(dst + 32), w.in_prev + off(g, w.xload, stream_row(w, rho - D)));
     cp_async_commit();
 }
 
@@ -258,7 +271,8 @@ __device__ __forceinline__ void stream_group(const StreamWarp& w, const Geo& g, 
 template <int S, bool PER, int T>
 __global__ void __launch_bounds__(kStreamWarps * 32)
     k5_stream(const float* __restrict__ in_cur, const float* __restrict__ in_prev, float* __restrict__ out_cur,
-              float* __restrict__ out_prev, Geo g, Coef3<float> a, int strips_x, int n_strips, int L) {
+              float* __restrict__ out_prev, Geo g, Coef3<float> a, int strips_x, int n_strips, int L,
+              int wrap) {
     using C = StreamCfg<S, T>;
     constexpr int R = C::R, D = C::D, WIN = C::WIN, HX = C::HX, OW = C::OW, NB = C::NB, PF = C::PF;
     extern __shared__ float4 stream_smem[];
@@ -277,6 +291,9 @@ __global__ void __launch_bounds__(kStreamWarps * 32)
     w.xload = min(w.xl, g.pitch - g.G - 4);     // inside the row's storage; clamped lanes are
                                                 // more than R T columns right of the grid
     w.ymax = g.ny + g.G - 1;                    // last stored row
+    w.ny = g.ny;
+    w.wrap = PER && wrap;                       // nx % 4 == 0: a wrapped vector stays whole
+    if (w.wrap) w.xload = ((w.xl % g.nx) + g.nx) % g.nx;
     w.rho0 = y0 - R * T;                        // first input row (>= -G)
     w.nsteps = L + T * (D + R);
 #pragma unroll

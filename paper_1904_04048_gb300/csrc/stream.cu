@@ -8,6 +8,17 @@
 
 namespace w2d {
 
+// Periodic images of planes p and q in the first gw rings.
+static int ring_images(wave2d* h, int p, int q) {
+    // grid: x spans a band row, y = 2 gw band rows + the side-band blocks
+    const int gx = std::min((h->nx + 2 * h->gw + 255) / 256, 16);
+    const int side = std::max(1, std::min((h->ny * 2 * h->gw + 255) / 256 / gx, 64));
+    k5_ring_images<<<dim3(gx, 2 * h->gw + side, 2), 256, 0, h->stream>>>(
+        static_cast<float*>(h->hi[p]), static_cast<float*>(h->hi[q]), h->geo(), h->gw);
+    W2D_LAUNCHED("periodic image kernel launch");
+    return WAVE2D_OK;
+}
+
 template <int S, bool PER, int T>
 static int launch_stream_t(wave2d* h) {
     using C = StreamCfg<S, T>;
@@ -20,17 +31,20 @@ static int launch_stream_t(wave2d* h) {
     // the levels move to the other pair with their roles kept (plane p -> p ^ 2)
     const int oc = h->cur ^ 2, op = h->prv ^ 2;
     const Coef3<float> a{(float)h->a[0], (float)h->a[1], (float)h->a[2]};
+    // periodic grids whose rows are whole vectors: inputs read at wrapped
+    // coordinates, images rebuilt once before a ring reader runs
+    const bool wrap = PER && h->nx % 4 == 0 && h->ny >= 16;
     kern<<<(n + kStreamWarps - 1) / kStreamWarps, kStreamWarps * 32, smem, h->stream>>>(
         static_cast<const float*>(h->hi[h->cur]), static_cast<const float*>(h->hi[h->prv]),
-        static_cast<float*>(h->hi[oc]), static_cast<float*>(h->hi[op]), h->geo(), a, strips_x, n, L);
+        static_cast<float*>(h->hi[oc]), static_cast<float*>(h->hi[op]), h->geo(), a, strips_x, n, L, (int)wrap);
     W2D_LAUNCHED("streaming temporal kernel launch");
-    if constexpr (PER) {  // periodic images of both output levels in the first gw rings
-        // grid: x spans a band row, y = 2 gw band rows + the side-band blocks
-        const int gx = std::min((h->nx + 2 * h->gw + 255) / 256, 16);
-        const int side = std::max(1, std::min((h->ny * 2 * h->gw + 255) / 256 / gx, 64));
-        k5_ring_images<<<dim3(gx, 2 * h->gw + side, 2), 256, 0, h->stream>>>(
-            static_cast<float*>(h->hi[oc]), static_cast<float*>(h->hi[op]), h->geo(), h->gw);
-        W2D_LAUNCHED("periodic image kernel launch");
+    if constexpr (PER) {
+        if (wrap) {
+            h->rings_stale = true;
+        } else {
+            int rc = ring_images(h, oc, op);
+            if (rc != WAVE2D_OK) return rc;
+        }
     }
     h->cur = oc;
     h->prv = op;
@@ -49,6 +63,12 @@ static int launch_stream_sp(wave2d* h) {
 template <int S>
 static int launch_stream_s(wave2d* h) {
     return (h->bc == WAVE2D_BC_PERIODIC) ? launch_stream_sp<S, true>(h) : launch_stream_sp<S, false>(h);
+}
+
+int stream_fresh_rings(wave2d* h) {
+    if (!h->rings_stale) return WAVE2D_OK;
+    h->rings_stale = false;
+    return ring_images(h, h->cur, h->prv);
 }
 
 int stream_launch(wave2d* h) {

@@ -466,8 +466,16 @@ static int launch_temporal(wave2d* h) {
 // remain, else one level.  Returns the number of levels advanced (< 0: error).
 static int launch_block(wave2d* h, int64_t remaining) {
     int rc;
-    if (is_multilevel(h->kernel) && remaining >= h->temporal_t) {
-        rc = (h->kernel == WAVE2D_KERNEL_STREAM) ? stream_launch(h) : launch_temporal(h);
+    if (h->kernel == WAVE2D_KERNEL_STREAM && remaining >= h->temporal_t) {
+        rc = stream_launch(h);
+        if (rc != WAVE2D_OK) return rc;
+        h->k += h->temporal_t;
+        return h->temporal_t;
+    }
+    rc = stream_fresh_rings(h);  // the kernels below read the ghost rings
+    if (rc != WAVE2D_OK) return rc;
+    if (h->kernel == WAVE2D_KERNEL_TEMPORAL && remaining >= h->temporal_t) {
+        rc = launch_temporal(h);
         if (rc != WAVE2D_OK) return rc;
         h->k += h->temporal_t;
         return h->temporal_t;
@@ -587,6 +595,7 @@ static int run_graph(wave2d* h, int64_t& n) {
             }
             done += adv;
         }
+        if (rc == WAVE2D_OK) rc = stream_fresh_rings(h);  // a replay ends with valid rings
         const int64_t launched = g_launches.load() - before;
         cudaError_t e = cudaStreamEndCapture(h->stream, &g);
         g_launches.store(before);  // captured launches run only when the graph does
@@ -1009,7 +1018,7 @@ int wave2d_step_n(wave2d_t h, int64_t n) {
         if (adv < 0) return adv;
         n -= adv;
     }
-    return WAVE2D_OK;
+    return stream_fresh_rings(h);
 }
 
 int wave2d_error_vs_exact(wave2d_t h, const wave2d_exact* ex, double* rel_l2, double* rel_linf,

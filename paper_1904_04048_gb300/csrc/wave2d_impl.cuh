@@ -92,6 +92,7 @@ struct wave2d {
     // state
     int cur = 0, prv = 1;  // planes holding u^k and u^{k-1}
     int gw = 1;            // periodic image rings kept valid by every writer
+    bool rings_stale = false;  // streaming launches left the current rings unwritten (see stream.cu)
     int64_t k = 0;
     bool initialized = false;
     bool tracking = false;
@@ -124,7 +125,11 @@ int chain_tma_step(wave2d* h);
 void chain_tma_box(const wave2d* h, int& box_w, int& box_h, int& tile_w, int& tile_h);
 // Register-streaming temporal kernel (stream.cu): T levels of a handle whose
 // kernel is WAVE2D_KERNEL_STREAM, out of place into the other pair of planes.
+// On periodic grids it may leave the current levels' ghost rings stale
+// (rings_stale); stream_fresh_rings rebuilds them and must run before any
+// other kernel reads the planes' rings and before a library call returns.
 int stream_launch(wave2d* h);
+int stream_fresh_rings(wave2d* h);
 // Guard-band canaries (canary.cu): fill the untouched cells of every plane
 // when the handle has WAVE2D_CANARY.
 int canary_fill(wave2d* h);

@@ -2,8 +2,9 @@
 the CPU: for ragged and degenerate grids, every strip height the tuning
 accepts near the edges and every scheme and depth, each global load stays in
 the level plane (ghost ring and row padding included) at a 16-byte aligned
-address, the cp.async ring slots stay in the CTA's shared memory, and the
-stored vectors cover every grid node exactly once.
+address (on periodic grids read at wrapped coordinates: inside the grid, at
+the node the periodic image holds), the cp.async ring slots stay in the CTA's
+shared memory, and the stored vectors cover every grid node exactly once.
 
 The model restates the kernel's constants and formulas (kernels_stream.cuh):
 strips of 32 C columns (C = 4 nodes per lane) with HX = R T rounded up to a
@@ -26,7 +27,17 @@ def plane_geometry(nx, ny):
     return pitch, ny + 2 * G
 
 
-def replay(nx, ny, scheme, T, L):
+def stream_row(y, ny, ymax, wrap):
+    if not wrap:
+        return min(y, ymax)
+    if y < 0:
+        return y + ny
+    if y < ny:
+        return y
+    return y - ny if y - ny < ny else y % ny
+
+
+def replay(nx, ny, scheme, T, L, periodic=False):
     R = 2 if scheme == 13 else 1
     HX = (R * T + 3) // 4 * 4
     W = 32 * C
@@ -39,6 +50,7 @@ def replay(nx, ny, scheme, T, L):
     def off(i, j):
         return (j + G) * pitch + (i + G)
 
+    wrap = periodic and nx % 4 == 0 and ny >= 16   # the launcher's condition
     covered = {}
     for strip in range(strips_x * strips_y):
         warp = strip % WARPS
@@ -47,12 +59,18 @@ def replay(nx, ny, scheme, T, L):
         for lane in range(32):
             xl = x0 - HX + C * lane
             xload = min(xl, pitch - G - C)
+            if wrap:
+                xload = xl % nx
+                assert xload + C <= nx                  # the wrapped vector stays whole
             assert xl >= -G
             for step in range(nsteps + PF):            # copies issued up to PF steps ahead
                 rho = rho0 + step
                 for y in (rho, rho - R):                # u^k row and u^{k-1} row
-                    o = off(xload, min(y, ymax))
+                    yr = stream_row(y, ny, ymax, wrap)
+                    o = off(xload, yr)
                     assert 0 <= o and o + C <= n_el and o % 4 == 0
+                    if wrap:                            # the node the periodic image holds
+                        assert 0 <= yr < ny and (yr - y) % ny == 0 and (xload - xl) % nx == 0
                 slot = step % NB
                 smem = ((warp * NB + slot) * 2 + 1) * 32 + lane   # plane 1 is the larger index
                 assert smem < WARPS * NB * 2 * 32
@@ -77,9 +95,10 @@ SHAPES = [(1, 1), (5, 3), (13, 31), (64, 64), (121, 1), (1, 200), (120, 17), (30
 @pytest.mark.parametrize("scheme", [5, 9, 13])
 @pytest.mark.parametrize("T", [2, 3, 4])
 @pytest.mark.parametrize("L", [8, 16, 37, 64])
-def test_loads_in_bounds_and_stores_cover_each_node_once(scheme, T, L):
-    for nx, ny in SHAPES:
-        replay(nx, ny, scheme, T, L)
+@pytest.mark.parametrize("periodic", [False, True], ids=["clamped", "periodic"])
+def test_loads_in_bounds_and_stores_cover_each_node_once(scheme, T, L, periodic):
+    for nx, ny in SHAPES + [(4, 16), (16, 17), (64, 20)]:
+        replay(nx, ny, scheme, T, L, periodic)
 
 
 def test_halo_reaches_every_dependency():
