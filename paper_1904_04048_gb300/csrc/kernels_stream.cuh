@@ -19,16 +19,18 @@
 //
 // Zero boundary: nodes outside the grid are forced to zero at every level
 // (their inputs come from the ghost ring, which holds zeros).  Periodic
-// boundary: the kernel stores grid nodes only.  When nx is a multiple of 4 it
-// reads its inputs at wrapped coordinates (a lane's 4-node vector wraps as a
-// whole; rows wrap per step), so the ghost ring is neither read nor kept up
-// to date between launches, and k5_ring_images rebuilds the images once,
-// before a kernel that reads the ring runs (the caller tracks this).
-// Otherwise the inputs' ghost ring holds periodic images at least R (T + 1)
-// rows and HX columns deep and k5_ring_images copies them after every launch.
-// (Measured on GB300 at 4096^2: image stores inside the kernel made the
-// 13-point level 23.0 us instead of 19.5 with a copy per launch; the copy
-// itself was 7 % of the device time.)
+// boundary: the kernel stores grid nodes only.  The WRAP variant (5 and 9
+// points, nx a multiple of 4) reads its inputs at wrapped coordinates (a
+// lane's 4-node vector wraps as a whole, rows wrap per step), so the ghost
+// ring is neither read nor kept up to date between launches and
+// k5_ring_images rebuilds the images once, before a kernel that reads the
+// ring runs (the caller tracks this).  Otherwise the inputs' ghost ring holds
+// periodic images at least R (T + 1) rows and HX columns deep and
+// k5_ring_images copies them after every launch.  (Measured on GB300 at
+// 4096^2: image stores inside the kernel made the 13-point level 23.0 us
+// instead of 19.5 with a copy per launch, the copies 7 % of the device time;
+// wrapped reads saved the copies of the 9-point kernel but slowed the
+// 13-point kernel by 12 %.)
 #pragma once
 #include <utility>
 
@@ -162,7 +164,6 @@ struct StreamWarp {
     float* out_prev;
     float4* ring;     // this warp's input row slots: slot b, plane p at ring[(2 b + p) * 32]
     int lane, xl, xload, ymax, rho0, nsteps, ny;
-    bool wrap;  // periodic inputs read at wrapped coordinates (the ghost ring is not read)
     bool outlane, interior;
     bool colin[4];
 };
@@ -170,21 +171,26 @@ struct StreamWarp {
 // Copy input step `step` (u^k row rho0 + step, u^{k-1} row rho0 + step - D)
 // into its ring slot and close the copy group.  Rows past the stored band are
 // clamped to its last row (their values reach no stored node).
-// Stored row of input row y: clamped to the stored band, or wrapped.
+// Stored row of input row y: clamped to the stored band, or (WRAP) wrapped
+// by selects.  Wrapped rows y >= 2 ny, which only strips taller than the grid
+// reach and no stored node depends on, read row ny - 1.
+template <bool WRAP>
 __device__ __forceinline__ int stream_row(const StreamWarp& w, int y) {
-    if (!w.wrap) return min(y, w.ymax);
-    if (y < 0) return y + w.ny;  // y >= -R (T + 1) > -ny (ny >= 16 when wrapping)
-    if (y < w.ny) return y;
-    return y - w.ny < w.ny ? y - w.ny : y % w.ny;
+    if constexpr (!WRAP) {
+        return min(y, w.ymax);
+    } else {
+        const int r = y < 0 ? y + w.ny : y;  // y >= -R (T + 1) > -ny (ny >= 16 when wrapping)
+        return r >= w.ny ? min(r - w.ny, w.ny - 1) : r;
+    }
 }
 
-template <int D, int NB>
+template <int D, int NB, bool WRAP>
 __device__ __forceinline__ void stream_issue(const StreamWarp& w, const Geo& g, int step) {
     const int rho = w.rho0 + step;
     const int b = step % NB;
     float4* dst = w.ring + 2 * b * 32 + w.lane;
-    cp_async16(smem_u32(dst), w.in_cur + off(g, w.xload, stream_row(w, rho)));
-    cp_async16(smem_u32(dst + 32), w.in_prev + off(g, w.xload, stream_row(w, rho - D)));
+    cp_async16(smem_u32(dst), w.in_cur + off(g, w.xload, stream_row<WRAP>(w, rho)));
+    cp_async16(smem_u32(dst + 32), w.in_prev + off(g, w.xload, stream_row<WRAP>(w, rho - D)));
     cp_async_commit();
 }
 
@@ -214,7 +220,7 @@ __device__ __forceinline__ void stream_store_checked(const StreamWarp& w, const 
 // first T (D + R) steps) and steps past the end are skipped by warp-uniform
 // branches, and interior strips (full vectors, rows inside the grid) store
 // with predicated instructions.
-template <int S, bool PER, int T>
+template <int S, bool PER, int T, bool WRAP>
 __device__ __forceinline__ void stream_group(const StreamWarp& w, const Geo& g, const Coef3<float>& a, f2x a10x2,
                                              f2x a11x2, f2x a20x2, float (&q)[T][StreamCfg<S, T>::WIN][4],
                                              int base) {
@@ -230,7 +236,7 @@ __device__ __forceinline__ void stream_group(const StreamWarp& w, const Geo& g, 
         f4_to(src[0], q[0][s]);
         float pm[4];
         f4_to(src[32], pm);
-        stream_issue<D, NB>(w, g, step + PF);
+        stream_issue<D, NB, WRAP>(w, g, step + PF);
         float top[4];  // level T on row rho - T D
         static_for<T>([&](auto tc) {
             constexpr int t = decltype(tc)::value + 1;
@@ -268,11 +274,10 @@ __device__ __forceinline__ void stream_group(const StreamWarp& w, const Geo& g, 
 // that receive u^{k+T} and u^{k+T-1}.  Strip s covers output columns
 // [x0, x0 + OW) with x0 = (s % strips_x) OW and rows [y0, y0 + L) with
 // y0 = (s / strips_x) L.
-template <int S, bool PER, int T>
+template <int S, bool PER, int T, bool WRAP>
 __global__ void __launch_bounds__(kStreamWarps * 32)
     k5_stream(const float* __restrict__ in_cur, const float* __restrict__ in_prev, float* __restrict__ out_cur,
-              float* __restrict__ out_prev, Geo g, Coef3<float> a, int strips_x, int n_strips, int L,
-              int wrap) {
+              float* __restrict__ out_prev, Geo g, Coef3<float> a, int strips_x, int n_strips, int L) {
     using C = StreamCfg<S, T>;
     constexpr int R = C::R, D = C::D, WIN = C::WIN, HX = C::HX, OW = C::OW, NB = C::NB, PF = C::PF;
     extern __shared__ float4 stream_smem[];
@@ -292,8 +297,7 @@ __global__ void __launch_bounds__(kStreamWarps * 32)
                                                 // more than R T columns right of the grid
     w.ymax = g.ny + g.G - 1;                    // last stored row
     w.ny = g.ny;
-    w.wrap = PER && wrap;                       // nx % 4 == 0: a wrapped vector stays whole
-    if (w.wrap) w.xload = ((w.xl % g.nx) + g.nx) % g.nx;
+    if constexpr (WRAP) w.xload = ((w.xl % g.nx) + g.nx) % g.nx;  // nx % 4 == 0: the vector stays whole
     w.rho0 = y0 - R * T;                        // first input row (>= -G)
     w.nsteps = L + T * (D + R);
 #pragma unroll
@@ -312,11 +316,11 @@ __global__ void __launch_bounds__(kStreamWarps * 32)
 #pragma unroll
             for (int e = 0; e < 4; ++e) q[t][s][e] = 0.0f;
 #pragma unroll
-    for (int s = 0; s < PF; ++s) stream_issue<D, NB>(w, g, s);
+    for (int s = 0; s < PF; ++s) stream_issue<D, NB, WRAP>(w, g, s);
 
 #pragma unroll 1
     for (int base = 0; base < w.nsteps; base += WIN)
-        stream_group<S, PER, T>(w, g, a, a10x2, a11x2, a20x2, q, base);
+        stream_group<S, PER, T, WRAP>(w, g, a, a10x2, a11x2, a20x2, q, base);
     cp_async_wait_all();  // no copy may land in shared memory after the warp exits
 }
 

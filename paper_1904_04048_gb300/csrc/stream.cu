@@ -19,10 +19,10 @@ static int ring_images(wave2d* h, int p, int q) {
     return WAVE2D_OK;
 }
 
-template <int S, bool PER, int T>
+template <int S, bool PER, int T, bool WRAP>
 static int launch_stream_t(wave2d* h) {
     using C = StreamCfg<S, T>;
-    auto kern = k5_stream<S, PER, T>;
+    auto kern = k5_stream<S, PER, T, WRAP>;
     constexpr int smem = stream_smem_bytes<S, T>();
     const int strips_x = (h->nx + C::OW - 1) / C::OW;
     const int L = h->temporal_oh;  // rows per strip
@@ -31,33 +31,39 @@ static int launch_stream_t(wave2d* h) {
     // the levels move to the other pair with their roles kept (plane p -> p ^ 2)
     const int oc = h->cur ^ 2, op = h->prv ^ 2;
     const Coef3<float> a{(float)h->a[0], (float)h->a[1], (float)h->a[2]};
-    // periodic grids whose rows are whole vectors: inputs read at wrapped
-    // coordinates, images rebuilt once before a ring reader runs
-    const bool wrap = PER && h->nx % 4 == 0 && h->ny >= 16;
     kern<<<(n + kStreamWarps - 1) / kStreamWarps, kStreamWarps * 32, smem, h->stream>>>(
         static_cast<const float*>(h->hi[h->cur]), static_cast<const float*>(h->hi[h->prv]),
-        static_cast<float*>(h->hi[oc]), static_cast<float*>(h->hi[op]), h->geo(), a, strips_x, n, L, (int)wrap);
+        static_cast<float*>(h->hi[oc]), static_cast<float*>(h->hi[op]), h->geo(), a, strips_x, n, L);
     W2D_LAUNCHED("streaming temporal kernel launch");
-    if constexpr (PER) {
-        if (wrap) {
-            h->rings_stale = true;
-        } else {
-            int rc = ring_images(h, oc, op);
-            if (rc != WAVE2D_OK) return rc;
-        }
+    if constexpr (WRAP) {
+        h->rings_stale = true;  // images rebuilt once before a ring reader runs
+    } else if constexpr (PER) {
+        int rc = ring_images(h, oc, op);
+        if (rc != WAVE2D_OK) return rc;
     }
     h->cur = oc;
     h->prv = op;
     return WAVE2D_OK;
 }
 
+template <int S, bool PER, bool WRAP>
+static int launch_stream_spw(wave2d* h) {
+    switch (h->temporal_t) {
+        case 2: return launch_stream_t<S, PER, 2, WRAP>(h);
+        case 3: return launch_stream_t<S, PER, 3, WRAP>(h);
+        default: return launch_stream_t<S, PER, 4, WRAP>(h);
+    }
+}
+
+// Periodic 5- and 9-point grids whose rows are whole vectors read their
+// inputs at wrapped coordinates (WRAP); the 13-point kernel keeps the ghost
+// ring (wrapping measured 12 % slower there).
 template <int S, bool PER>
 static int launch_stream_sp(wave2d* h) {
-    switch (h->temporal_t) {
-        case 2: return launch_stream_t<S, PER, 2>(h);
-        case 3: return launch_stream_t<S, PER, 3>(h);
-        default: return launch_stream_t<S, PER, 4>(h);
+    if constexpr (PER && S != 13) {
+        if (h->nx % 4 == 0 && h->ny >= 16) return launch_stream_spw<S, PER, true>(h);
     }
+    return launch_stream_spw<S, PER, false>(h);
 }
 
 template <int S>

@@ -30,11 +30,8 @@ def plane_geometry(nx, ny):
 def stream_row(y, ny, ymax, wrap):
     if not wrap:
         return min(y, ymax)
-    if y < 0:
-        return y + ny
-    if y < ny:
-        return y
-    return y - ny if y - ny < ny else y % ny
+    r = y + ny if y < 0 else y
+    return min(r - ny, ny - 1) if r >= ny else r
 
 
 def replay(nx, ny, scheme, T, L, periodic=False):
@@ -50,7 +47,7 @@ def replay(nx, ny, scheme, T, L, periodic=False):
     def off(i, j):
         return (j + G) * pitch + (i + G)
 
-    wrap = periodic and nx % 4 == 0 and ny >= 16   # the launcher's condition
+    wrap = periodic and scheme != 13 and nx % 4 == 0 and ny >= 16   # the launcher's condition
     covered = {}
     for strip in range(strips_x * strips_y):
         warp = strip % WARPS
@@ -70,7 +67,8 @@ def replay(nx, ny, scheme, T, L, periodic=False):
                     o = off(xload, yr)
                     assert 0 <= o and o + C <= n_el and o % 4 == 0
                     if wrap:                            # the node the periodic image holds
-                        assert 0 <= yr < ny and (yr - y) % ny == 0 and (xload - xl) % nx == 0
+                        assert 0 <= yr < ny and (xload - xl) % nx == 0
+                        assert (yr - y) % ny == 0 or y >= 2 * ny   # rows past 2 ny feed no stored node
                 slot = step % NB
                 smem = ((warp * NB + slot) * 2 + 1) * 32 + lane   # plane 1 is the larger index
                 assert smem < WARPS * NB * 2 * 32
