@@ -54,20 +54,28 @@ KSHORT = {1: "simple", 2: "tma", 3: "temporal", 4: "stream"}
 
 # DRAM bytes (read + write) of one launch of a kernel at the benchmark size,
 # from an ncu capture of the same kernel source (see the profiles directory),
-# keyed by (kernel, hash of the kernel sources, scheme, tile rows) so that a
-# figure is dropped once the kernel or the autotuner's choice changes.
-NCU_TRAFFIC = {("k5_stream", "c8c89914c5b3aac3", 9, 16): 146468608 + 93931264,
-               ("k5_stream", "c8c89914c5b3aac3", 13, 32): 190684416 + 94103808,
-               ("k2_tma", "c8c89914c5b3aac3", 13, 0): 135371264 + 20168448}
+# keyed by (kernel, hash of that kernel's sources, scheme, rows per tile or
+# strip) so that a figure is dropped once the kernel or the autotuner's choice
+# changes.
+NCU_TRAFFIC = {("k5_stream", "c8d48361198f8b68", 9, 16): 171168256 + 92256512,
+               ("k5_stream", "c8d48361198f8b68", 9, 48): 176076544 + 91702784,
+               ("k5_stream", "c8d48361198f8b68", 13, 32): 194497280 + 92939520,
+               ("k5_stream", "c8d48361198f8b68", 13, 48): 192406528 + 92010752,
+               ("k2_tma", "6d22d695e356831d", 13, 0): 135366144 + 19828224}
+
+# Sources each kernel is built from (the hash keys of NCU_TRAFFIC).
+KERNEL_SOURCES = {"k2_tma": ("kernels.cuh", "stencil_ops.cuh"),
+                  "k3_temporal": ("kernels.cuh", "kernels_temporal.cuh", "stencil_ops.cuh"),
+                  "k5_stream": ("kernels.cuh", "kernels_stream.cuh", "stencil_ops.cuh")}
 
 # The autotuner's choice on GB300 (kernel, T = 4, rows per tile or strip),
 # used by --fixed-tuning for profiler runs.
 FIXED_TUNING = {9: ("stream", 48), 13: ("stream", 32)}
 
 
-def kernel_source_hash() -> str:
+def kernel_source_hash(kernel: str) -> str:
     hsh = hashlib.sha256()
-    for f in ("kernels.cuh", "kernels_temporal.cuh", "kernels_stream.cuh", "stencil_ops.cuh"):
+    for f in KERNEL_SOURCES.get(kernel, ()):
         with open(os.path.join(ROOT, "paper_1904_04048_gb300", "csrc", f), "rb") as fh:
             hsh.update(fh.read())
     return hsh.hexdigest()[:16]
@@ -379,7 +387,6 @@ def run_ours(args, rank, world, local_rank):
         return None
 
     peak, peak_src = measured_peaks()
-    src_hash = kernel_source_hash()
     per_scheme_stepn = {s: sum(a.elapsed_time(b) for ss, a, b in timing if ss == s) / 1e3 for s in SCHEMES}
     clocks = clk.summary()
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
@@ -403,7 +410,8 @@ def run_ours(args, rank, world, local_rank):
         avg_launch = total / n_launch
         alg_bytes = (16 if T > 1 else 12) * N * N  # read the two levels, write two (one for one step)
         achieved = alg_bytes / avg_launch / 1e9
-        per = [NCU_TRAFFIC.get((kname, src_hash, s, tuned[s]["tile_h"] if T > 1 else 0)) for s in ss]
+        per = [NCU_TRAFFIC.get((kname, kernel_source_hash(kname), s, tuned[s]["tile_h"] if T > 1 else 0))
+               for s in ss]
         traffic = int(sum(per) / len(per)) if all(per) else None  # mean over the schemes' launches
         label = f"{kname} (FP32, T={T}, {'/'.join(str(s) for s in ss)}-point)"
         hbm_view = {"bound": "hbm", "kernel": label, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
@@ -453,7 +461,7 @@ def run_ours(args, rank, world, local_rank):
         "one_step_kernel": ({"kernel": "k2_tma", "avg_launch_us": {str(s): round(one_step[s] * 1e6, 3) for s in SCHEMES},
                              "frac": {str(s): round(12 * N * N / one_step[s] / 1e9 / peak, 4) for s in SCHEMES},
                              "algorithmic_bytes_per_launch": 12 * N * N,
-                             "traffic": NCU_TRAFFIC.get(("k2_tma", src_hash, 13, 0))}
+                             "traffic": NCU_TRAFFIC.get(("k2_tma", kernel_source_hash("k2_tma"), 13, 0))}
                             if all(one_step[s] for s in SCHEMES) else None),
         "clocks": clocks,
         "result_norms": {str(s): [results[s][0], results[s][1]] for s in SCHEMES},
