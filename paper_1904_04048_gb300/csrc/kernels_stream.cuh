@@ -1,5 +1,6 @@
 // Register-streaming temporally blocked two-step (Eq. A2 applied T times per
-// HBM round trip, without shared memory).
+// HBM round trip; the levels live in registers, shared memory only stages the
+// input rows).
 //
 // Each warp owns a strip of 128 grid columns (four consecutive nodes per
 // lane) and L output rows, and walks down the strip one input row per step.
@@ -168,12 +169,10 @@ struct StreamWarp {
     bool colin[4];
 };
 
-// Copy input step `step` (u^k row rho0 + step, u^{k-1} row rho0 + step - D)
-// into its ring slot and close the copy group.  Rows past the stored band are
-// clamped to its last row (their values reach no stored node).
-// Stored row of input row y: clamped to the stored band, or (WRAP) wrapped
-// by selects.  Wrapped rows y >= 2 ny, which only strips taller than the grid
-// reach and no stored node depends on, read row ny - 1.
+// Stored row of input row y: clamped to the stored band (rows past it reach
+// no stored node), or (WRAP) wrapped by selects.  Wrapped rows y >= 2 ny,
+// which only strips taller than the grid reach and no stored node depends on,
+// read row ny - 1.
 template <bool WRAP>
 __device__ __forceinline__ int stream_row(const StreamWarp& w, int y) {
     if constexpr (!WRAP) {
@@ -184,6 +183,8 @@ __device__ __forceinline__ int stream_row(const StreamWarp& w, int y) {
     }
 }
 
+// Copy input step `step` (u^k row rho0 + step, u^{k-1} row rho0 + step - D)
+// into its ring slot and close the copy group.
 template <int D, int NB, bool WRAP>
 __device__ __forceinline__ void stream_issue(const StreamWarp& w, const Geo& g, int step) {
     const int rho = w.rho0 + step;
