@@ -361,6 +361,10 @@ class Wave2D:
         check(lib().wave2d_set_raw(self._h, buf.ctypes.data_as(ctypes.c_void_p), buf.size, int(k)))
 
     def set_tuning(self, kernel=KERNEL_AUTO, tile_h=0, temporal_t=0, use_graph=-1, ctas_per_sm=0):
+        """wave2d_set_tuning: ``kernel`` one of KERNEL_AUTO / SIMPLE / TMA /
+        TEMPORAL / STREAM; ``tile_h`` rows per tile (TEMPORAL: 16, 24, 32, 64)
+        or per strip (STREAM: 8 .. 4096), 0 = default; ``temporal_t`` levels
+        per launch of the two multi-level kernels (2, 3, 4; 0 = 4)."""
         t = wave2d_tune(int(kernel), int(tile_h), int(temporal_t), int(use_graph), int(ctas_per_sm))
         check(lib().wave2d_set_tuning(self._h, ctypes.byref(t)))
 
