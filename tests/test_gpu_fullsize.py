@@ -1,7 +1,8 @@
 """Parity at the full benchmark size, in the launch configuration the
 benchmark times (FP32 storage, 4096^2 periodic grid, lambda = 0.9 lambda_max,
 9- and 13-point schemes; the automatic kernel, which is the register-streaming
-kernel at this size, and the shared-memory temporal kernel the autotuner may
+kernel at this size, the streaming kernel with the strip heights bench.py
+--fixed-tuning pins, and the shared-memory temporal kernel the autotuner may
 choose instead).
 
 * Multi-pulse displacement plus band-limited velocity (the benchmark's
@@ -39,7 +40,7 @@ def bench_ic():
 
 
 @pytest.mark.parametrize("scheme", [9, 13])
-@pytest.mark.parametrize("kernel", ["auto", "temporal"])
+@pytest.mark.parametrize("kernel", ["auto", "temporal", "bench-fixed"])
 def test_benchmark_inputs_against_oracle(w, orc, bench_ic, scheme, kernel):
     u0, v0 = bench_ic
     h = 1.0 / N
@@ -48,8 +49,14 @@ def test_benchmark_inputs_against_oracle(w, orc, bench_ic, scheme, kernel):
     with w.Wave2D(N, N, h, lam * h, scheme=scheme, bc=BC_PERIODIC, dtype=1) as sim:
         if kernel == "auto":
             assert sim.info().kernel == w.KERNEL_STREAM  # automatic choice at this size
-        else:
+        elif kernel == "temporal":
             sim.set_tuning(kernel=w.KERNEL_TEMPORAL, temporal_t=4)
+        else:  # the strips bench.py --fixed-tuning pins (the autotuner's usual choice)
+            from bench import FIXED_TUNING
+            name, rows = FIXED_TUNING[scheme]
+            assert name == "stream"
+            sim.set_tuning(kernel=w.KERNEL_STREAM, temporal_t=4, tile_h=rows)
+            assert sim.info().kernel == w.KERNEL_STREAM
         sim.first_step(u0, v0)
         sim.step_n(steps - 1)
         up, uc, _ = sim.get_state()
