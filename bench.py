@@ -69,9 +69,9 @@ KERNEL_SOURCES = {"k2_tma": ("kernels.cuh", "stencil_ops.cuh"),
                   "k3_temporal": ("kernels.cuh", "kernels_temporal.cuh", "stencil_ops.cuh"),
                   "k5_stream": ("kernels.cuh", "kernels_stream.cuh", "stencil_ops.cuh")}
 
-# The autotuner's choice on GB300 (kernel, T = 4, rows per tile or strip),
-# used by --fixed-tuning for profiler runs.
-FIXED_TUNING = {9: ("stream", 48), 13: ("stream", 32)}
+# The autotuner's choice on GB300 (kernel, rows per tile or strip, levels
+# per launch), used by --fixed-tuning for profiler runs.
+FIXED_TUNING = {9: ("stream", 64, 6), 13: ("stream", 64, 4)}
 
 
 def strip_comments(src: str) -> str:
@@ -293,9 +293,10 @@ def run_ours(args, rank, world, local_rank):
     for s in SCHEMES:
         sims[s].first_step(du0, dv0)
         if args.fixed_tuning:  # the autotuner's choice on the measured runs
-            kern = w.KERNEL_STREAM if FIXED_TUNING[s][0] == "stream" else w.KERNEL_TEMPORAL
-            sims[s].set_tuning(kernel=kern, temporal_t=4, tile_h=FIXED_TUNING[s][1])
-            best = w.wave2d_tune(kern, FIXED_TUNING[s][1], 4, -1, 0)
+            kname, rows, depth = FIXED_TUNING[s]
+            kern = w.KERNEL_STREAM if kname == "stream" else w.KERNEL_TEMPORAL
+            sims[s].set_tuning(kernel=kern, temporal_t=depth, tile_h=rows)
+            best = w.wave2d_tune(kern, rows, depth, -1, 0)
         else:
             best = sims[s].autotune(steps=64)
         tuned[s] = {"kernel": KSHORT[best.kernel],
@@ -699,14 +700,14 @@ def measure_diff_sums(w, torch, u0, v0, peak):
     return out
 
 
-def profile_case(kernel: str, scheme: int, segment: int = 28, tile_h: int = 32):
+def profile_case(kernel: str, scheme: int, segment: int = 28, tile_h: int = 32, depth: int = 4):
     """A short run of one kernel at the benchmark size, for profiler captures:
     the first step, then a few launches of the named kernel on the
     benchmark's inputs (no timing, no JSON line).  4096^2 FP32 holds about
     0.5 GB on the device.
       k2_tma:      4 one-step launches (the first step comes before them)
       k3_temporal: 3 launches of T = 4 levels, tile_h-row tiles
-      k5_stream:   3 launches of T = 4 levels, tile_h-row strips
+      k5_stream:   3 launches of T = depth levels, tile_h-row strips
       kc2_tma:     4 one-step launches of a derived scheme (``segment``)"""
     from initial_data import BC_PERIODIC, LAMBDA_MAX, pulses_and_noise
     from paper_1904_04048_gb300 import wave2d as w
@@ -722,8 +723,8 @@ def profile_case(kernel: str, scheme: int, segment: int = 28, tile_h: int = 32):
             sim.set_tuning(kernel=w.KERNEL_TMA, use_graph=0)
             levels = 4
         elif kernel == "k5_stream":
-            sim.set_tuning(kernel=w.KERNEL_STREAM, temporal_t=4, tile_h=tile_h, use_graph=0)
-            levels = 12
+            sim.set_tuning(kernel=w.KERNEL_STREAM, temporal_t=depth, tile_h=tile_h, use_graph=0)
+            levels = 3 * depth
         else:
             sim.set_tuning(kernel=w.KERNEL_TEMPORAL, temporal_t=4, tile_h=tile_h, use_graph=0)
             levels = 12
@@ -785,10 +786,12 @@ def main():
                     help="run a short case of one kernel for a profiler capture and exit")
     ap.add_argument("--profile-scheme", type=int, choices=[5, 9, 13], default=13)
     ap.add_argument("--profile-segment", type=int, default=28, help="derived scheme for kc2_tma")
-    ap.add_argument("--profile-tile", type=int, default=32, help="rows per tile for k3_temporal")
+    ap.add_argument("--profile-tile", type=int, default=32, help="rows per tile or strip (k3_temporal, k5_stream)")
+    ap.add_argument("--profile-depth", type=int, default=4, help="levels per launch of k5_stream")
     args = ap.parse_args()
     if args.profile_case:
-        profile_case(args.profile_case, args.profile_scheme, args.profile_segment, args.profile_tile)
+        profile_case(args.profile_case, args.profile_scheme, args.profile_segment, args.profile_tile,
+                     args.profile_depth)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

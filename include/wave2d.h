@@ -170,10 +170,11 @@ typedef struct {
     int32_t tile_h;       /* output rows per tile of WAVE2D_KERNEL_TEMPORAL: 16,
                              24, 32 or 64 (0 = 24 for 9 points, else 32); output
                              rows per strip of WAVE2D_KERNEL_STREAM: 8 .. 4096
-                             (0 = 16 R below 2^25 nodes, else 48; R the stencil
-                             radius)                                              */
+                             (0 = 64)                                             */
     int32_t temporal_t;   /* steps per launch of the multi-level kernels: 2, 3 or
-                             4; 0 = 4                                             */
+                             4 for WAVE2D_KERNEL_TEMPORAL (0 = 4); 2, 3, 4 or 6
+                             for WAVE2D_KERNEL_STREAM (0 = 4 for 13 points, 6
+                             for 5 and 9 points)                                  */
     int32_t use_graph;    /* capture runs of steps in a CUDA graph: 1 on, 0 off,
                              -1 automatic                                         */
     int32_t ctas_per_sm;  /* resident CTAs per SM for the TMA kernels; 0 = auto:
@@ -373,7 +374,10 @@ const char *wave2d_last_error(void);
  * that every GPU loading the library holds until the process exits.  Limits:
  * 1 <= nx, ny <= 8192, else WAVE2D_ERR_ARG.  The first call on each device
  * looks up the array's address (cudaGetSymbolAddress) and caches it: make
- * that first call before any stream capture.  All calls share the array and
+ * that first call before any stream capture.  The cached address belongs to
+ * the device's context of that moment: after cudaDeviceReset (or anything
+ * else that destroys the primary context) it is stale, so do not call this
+ * function again in that process.  All calls share the array and
  * it keeps the last call's contents (the call clears what must start at
  * zero): calls that overlap on the GPU, from any thread or stream, race and
  * must be serialised by the caller. */

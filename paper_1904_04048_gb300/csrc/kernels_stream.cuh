@@ -20,18 +20,17 @@
 //
 // Zero boundary: nodes outside the grid are forced to zero at every level
 // (their inputs come from the ghost ring, which holds zeros).  Periodic
-// boundary: the kernel stores grid nodes only.  The WRAP variant (5 and 9
-// points, nx a multiple of 4) reads its inputs at wrapped coordinates (a
-// lane's 4-node vector wraps as a whole, rows wrap per step), so the ghost
-// ring is neither read nor kept up to date between launches and
-// k5_ring_images rebuilds the images once, before a kernel that reads the
-// ring runs (the caller tracks this).  Otherwise the inputs' ghost ring holds
-// periodic images at least R (T + 1) rows and HX columns deep and
-// k5_ring_images copies them after every launch.  (Measured on GB300 at
-// 4096^2: image stores inside the kernel made the 13-point level 23.0 us
-// instead of 19.5 with a copy per launch, the copies 7 % of the device time;
-// wrapped reads saved the copies of the 9-point kernel but slowed the
-// 13-point kernel by 12 %.)
+// boundary: the kernel stores grid nodes only.  The WRAP variant (nx a
+// multiple of 4, ny >= 16) reads its inputs at wrapped coordinates (a lane's
+// 4-node vector wraps as a whole, rows wrap per step), so the ghost ring is
+// neither read nor kept up to date between launches and k5_ring_images
+// rebuilds the images once, before a kernel that reads the ring runs (the
+// caller tracks this).  Otherwise the inputs' ghost ring holds periodic
+// images at least R (T + 1) rows and HX columns deep and k5_ring_images
+// copies them after every launch.  (Measured on GB300 at 4096^2: image
+// stores inside the kernel made the 13-point level 23.0 us instead of 19.5
+// with a copy per launch; wrapped reads with 64-row strips take it to 16.9,
+// the copy kernel's 4.3-5.3 us per launch gone.)
 #pragma once
 #include <utility>
 
@@ -47,9 +46,15 @@ struct StreamCfg {
     static constexpr int HX = (R * T + 3) / 4 * 4;      // halo columns per side
     static constexpr int OW = 128 - 2 * HX;             // output columns per strip
     static constexpr int HL = HX / 4;                   // halo lanes per side
-    static constexpr int NB = 8;                        // input row slots per warp in shared memory
-    static constexpr int PF = 6;                        // rows copied ahead of the step that uses them
-    static_assert(R * T <= 16 && HX <= 16, "halo must fit the ghost ring");
+    // Input row slots per warp in shared memory and rows copied ahead of the
+    // step that uses them.  The 5- and 9-point kernels take a ring of 4 (2
+    // rows ahead): their 72-108 registers would allow 5-7 CTAs per SM, and
+    // the 8-slot ring's 32 KB per CTA held them to 6 (measured on GB300 at
+    // 4096^2: 9-point T = 4 level 14.4 -> 13.4 us).  The 13-point kernel is
+    // held to 4 CTAs per SM by its registers and keeps 8 slots, 6 ahead.
+    static constexpr int NB = (S == 13) ? 8 : 4;
+    static constexpr int PF = NB - 2;
+    static_assert(R * T <= 16 && HX <= 16 && R * (T + 1) < 16, "halo must fit the ghost ring");
     static_assert(PF + 2 <= NB, "a slot is refilled two steps after its last read");
 };
 

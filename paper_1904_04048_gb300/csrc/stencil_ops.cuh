@@ -189,22 +189,24 @@ __device__ __forceinline__ void two_step_update_pair(const float* c, const float
                                                      float& o1) {
     static_assert(S == 9 || S == 13, "packed pair path is for the 9- and 13-point schemes");
     const f2x cc = pk2(c[e + 2], c[e + 3]);
-    const f2x m4c = mul2(cc, pk2(-4.0f, -4.0f));
+    const f2x m4 = pk2(-4.0f, -4.0f);
+    // Each class sum ends with the -4 u_ij term as one FMA, cc * (-4) + sum:
+    // -4 u_ij is exact, so this rounds once, exactly as the scalar path's
+    // sum + (-4 u_ij) does, and saves the separate product.
     // delta(1,0): (east + west) + (north + south)
     const f2x ew = pk2(__fadd_rn(c[e + 3], c[e + 1]), __fadd_rn(c[e + 4], c[e + 2]));
     const f2x ns = add2(pk2(up[e + 2], up[e + 3]), pk2(dn[e + 2], dn[e + 3]));
-    const f2x d10 = add2(add2(ew, ns), m4c);
+    const f2x d10 = fma2(cc, m4, add2(ew, ns));
     f2x L = mul2(a10, d10);
     // delta(1,1): (ne + sw) + (nw + se)
     const f2x nesw = pk2(__fadd_rn(up[e + 3], dn[e + 1]), __fadd_rn(up[e + 4], dn[e + 2]));
     const f2x nwse = pk2(__fadd_rn(up[e + 1], dn[e + 3]), __fadd_rn(up[e + 2], dn[e + 4]));
-    const f2x d11 = add2(add2(nesw, nwse), m4c);
+    const f2x d11 = fma2(cc, m4, add2(nesw, nwse));
     L = fma2(a11, d11, L);
     if constexpr (S == 13) {
         // delta(2,0): (ee + ww) + (nn + ss), all pairs even-aligned
-        const f2x d20 = add2(add2(add2(pk2(c[e + 4], c[e + 5]), pk2(c[e], c[e + 1])),
-                                  add2(pk2(up2[e + 2], up2[e + 3]), pk2(dn2[e + 2], dn2[e + 3]))),
-                             m4c);
+        const f2x d20 = fma2(cc, m4, add2(add2(pk2(c[e + 4], c[e + 5]), pk2(c[e], c[e + 1])),
+                                          add2(pk2(up2[e + 2], up2[e + 3]), pk2(dn2[e + 2], dn2[e + 3]))));
         L = fma2(a20, d20, L);
     }
     const f2x base = fma2(pk2(p0, p1), pk2(-1.0f, -1.0f), mul2(cc, pk2(2.0f, 2.0f)));

@@ -51,16 +51,16 @@ static int launch_stream_spw(wave2d* h) {
     switch (h->temporal_t) {
         case 2: return launch_stream_t<S, PER, 2, WRAP>(h);
         case 3: return launch_stream_t<S, PER, 3, WRAP>(h);
+        case 6: return launch_stream_t<S, PER, 6, WRAP>(h);
         default: return launch_stream_t<S, PER, 4, WRAP>(h);
     }
 }
 
-// Periodic 5- and 9-point grids whose rows are whole vectors read their
-// inputs at wrapped coordinates (WRAP); the 13-point kernel keeps the ghost
-// ring (wrapping measured 12 % slower there).
+// Periodic grids whose rows are whole vectors read their inputs at wrapped
+// coordinates (WRAP); the others keep the ghost ring and a copy per launch.
 template <int S, bool PER>
 static int launch_stream_sp(wave2d* h) {
-    if constexpr (PER && S != 13) {
+    if constexpr (PER) {
         if (h->nx % 4 == 0 && h->ny >= 16) return launch_stream_spw<S, PER, true>(h);
     }
     return launch_stream_spw<S, PER, false>(h);

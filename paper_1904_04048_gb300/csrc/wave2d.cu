@@ -539,16 +539,21 @@ static int select_kernel(wave2d* h) {
         if (rc != WAVE2D_OK) return rc;
     }
     if (want == WAVE2D_KERNEL_STREAM) {
-        h->temporal_t = h->tune.temporal_t > 0 ? h->tune.temporal_t : 4;
-        // rows per strip by default: 16 R below 2^25 nodes, else 48 (measured
-        // on GB300 at 4096^2 and 8192^2: the 2RT rows a strip recomputes at
-        // its start cost less than the latency that fewer, longer strips
-        // leave exposed, until the grid holds several waves of strips)
-        const int64_t nodes = (int64_t)h->nx * h->ny;
-        h->temporal_oh = h->tune.tile_h > 0 ? h->tune.tile_h : (nodes < (int64_t(1) << 25) ? 16 * h->R : 48);
+        // default depth: 6 levels per launch for the radius-1 schemes (their
+        // halo columns round up to 8 for any T in 5..8, so deeper blocking
+        // costs no extra columns; measured on GB300 at 4096^2: 9-point level
+        // 13.4 us at T = 4, 11.7 at T = 6), 4 for the 13-point scheme (its
+        // registers allow no deeper ring at 4 CTAs per SM)
+        const int tt = h->tune.temporal_t;
+        h->temporal_t = ((tt >= 2 && tt <= 4) || tt == 6) ? tt : (h->scheme == 13 ? 4 : 6);
+        // rows per strip by default: 64 (measured on GB300 at 4096^2: the
+        // 2RT rows a strip recomputes at its start cost less than the tail of
+        // a second wave of strips; 64 rows make one wave of 2368 strips there)
+        h->temporal_oh = h->tune.tile_h > 0 ? h->tune.tile_h : 64;
     }
     if (want == WAVE2D_KERNEL_TEMPORAL) {
-        h->temporal_t = h->tune.temporal_t > 0 ? h->tune.temporal_t : 4;
+        const int tt = h->tune.temporal_t;
+        h->temporal_t = (tt >= 2 && tt <= 4) ? tt : 4;
         // default tile rows: the autotuner's choice on GB300 (3 CTAs per SM for
         // the 9-point scheme, 2 for the others)
         h->temporal_oh = h->tune.tile_h > 0 ? h->tune.tile_h : (h->scheme == 9 ? 24 : 32);
@@ -572,13 +577,15 @@ static bool want_graph(const wave2d* h, int64_t n) {
     return n >= 64 && (int64_t)h->nx * h->ny <= (1 << 22);
 }
 
-constexpr int kGraphSteps = 32;
+constexpr int kGraphSteps = 48;
 
-// A graph of kGraphSteps levels (a multiple of 2 T) returns the levels to the
-// planes they started in, so one graph per starting (cur, prv) is replayed.
+// A graph of kGraphSteps levels (a multiple of 2 T for every depth the
+// multi-level kernels take) returns the levels to the planes they started
+// in, so one graph per starting (cur, prv) is replayed.
 static int run_graph(wave2d* h, int64_t& n) {
     const int key = h->cur * 4 + h->prv;
-    static_assert(kGraphSteps % 8 == 0, "graph length must be a multiple of 2T");
+    static_assert(kGraphSteps % 4 == 0 && kGraphSteps % 6 == 0 && kGraphSteps % 8 == 0 && kGraphSteps % 12 == 0,
+                  "graph length must be a multiple of 2T");
     if (!h->graph[key]) {
         const int cur0 = h->cur, prv0 = h->prv;
         const int64_t k0 = h->k;
@@ -903,8 +910,14 @@ int wave2d_set_tuning(wave2d_t h, const wave2d_tune* tune) {
     if (multi && h->nclass > 0)
         return set_error(WAVE2D_ERR_ARG,
                          "the temporal kernels cover the 5-, 9- and 13-point schemes with plain sums only");
-    if (multi && !(tune->temporal_t == 0 || (tune->temporal_t >= 2 && tune->temporal_t <= 4)))
-        return set_error(WAVE2D_ERR_ARG, "temporal_t must be 0 (auto), 2, 3 or 4 (got %d)", tune->temporal_t);
+    if (tune->kernel == WAVE2D_KERNEL_TEMPORAL &&
+        !(tune->temporal_t == 0 || (tune->temporal_t >= 2 && tune->temporal_t <= 4)))
+        return set_error(WAVE2D_ERR_ARG, "temporal_t of the tiled kernel must be 0 (auto), 2, 3 or 4 (got %d)",
+                         tune->temporal_t);
+    if (tune->kernel == WAVE2D_KERNEL_STREAM &&
+        !(tune->temporal_t == 0 || (tune->temporal_t >= 2 && tune->temporal_t <= 4) || tune->temporal_t == 6))
+        return set_error(WAVE2D_ERR_ARG, "temporal_t of the streaming kernel must be 0 (auto), 2, 3, 4 or 6 (got %d)",
+                         tune->temporal_t);
     if (tune->kernel == WAVE2D_KERNEL_TEMPORAL && !(tune->tile_h == 0 || tune->tile_h == 16 ||
                                                     tune->tile_h == 24 || tune->tile_h == 32 || tune->tile_h == 64))
         return set_error(WAVE2D_ERR_ARG, "temporal tile_h must be 0 (auto), 16, 24, 32 or 64 (got %d)", tune->tile_h);
@@ -1218,8 +1231,8 @@ int wave2d_autotune(wave2d_t h, int64_t steps, wave2d_tune* best) {
         add(WAVE2D_KERNEL_TMA, 0, 0, 2);
         for (int T : {2, 3, 4})
             for (int oh : {16, 24, 32, 64}) add(WAVE2D_KERNEL_TEMPORAL, oh, T, 0);
-        for (int T : {2, 3, 4})
-            for (int rows : {16, 24, 32, 48}) add(WAVE2D_KERNEL_STREAM, rows, T, 0);
+        for (int T : {2, 3, 4, 6})
+            for (int rows : {16, 24, 32, 48, 64}) add(WAVE2D_KERNEL_STREAM, rows, T, 0);
     } else if (h->dtype == WAVE2D_F64) {
         add(WAVE2D_KERNEL_TMA, 0, 0, 1);
         add(WAVE2D_KERNEL_TMA, 0, 0, 2);
@@ -1269,8 +1282,13 @@ int wave2d_autotune(wave2d_t h, int64_t steps, wave2d_tune* best) {
         if (rc == WAVE2D_OK) rc = refresh_ghosts(h);
         if (rc == WAVE2D_OK) rc = wave2d_step_n(h, std::min<int64_t>(steps, 8));  // warm-up
         if (rc != WAVE2D_OK) break;
+        // a multi-level candidate is timed on whole launches (a multiple of
+        // its depth), so the one-level steps that finish an uneven run do not
+        // count against it; candidates are compared per level
+        const int64_t depth = is_multilevel(h->kernel) ? h->temporal_t : 1;
+        const int64_t levels = std::max<int64_t>(depth, steps / depth * depth);
         cudaEventRecord(e0, h->stream);
-        rc = wave2d_step_n(h, steps);
+        rc = wave2d_step_n(h, levels);
         cudaEventRecord(e1, h->stream);
         if (rc != WAVE2D_OK) break;
         if (cudaEventSynchronize(e1) != cudaSuccess) {
@@ -1279,6 +1297,7 @@ int wave2d_autotune(wave2d_t h, int64_t steps, wave2d_tune* best) {
         }
         float ms = 0;
         cudaEventElapsedTime(&ms, e0, e1);
+        ms /= (float)levels;
         if (c == 0 || ms < best_ms) {
             best_ms = ms;
             chosen = cands[c];

@@ -53,9 +53,9 @@ def test_benchmark_inputs_against_oracle(w, orc, bench_ic, scheme, kernel):
             sim.set_tuning(kernel=w.KERNEL_TEMPORAL, temporal_t=4)
         else:  # the strips bench.py --fixed-tuning pins (the autotuner's usual choice)
             from bench import FIXED_TUNING
-            name, rows = FIXED_TUNING[scheme]
+            name, rows, depth = FIXED_TUNING[scheme]
             assert name == "stream"
-            sim.set_tuning(kernel=w.KERNEL_STREAM, temporal_t=4, tile_h=rows)
+            sim.set_tuning(kernel=w.KERNEL_STREAM, temporal_t=depth, tile_h=rows)
             assert sim.info().kernel == w.KERNEL_STREAM
         sim.first_step(u0, v0)
         sim.step_n(steps - 1)

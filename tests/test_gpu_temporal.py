@@ -59,12 +59,13 @@ def test_temporal_equals_single_steps_bitwise(w, scheme, bc, T, oh, shape):
 
 @pytest.mark.parametrize("scheme", [5, 9, 13])
 @pytest.mark.parametrize("bc", [BC_ZERO, BC_PERIODIC], ids=["zero", "periodic"])
-@pytest.mark.parametrize("T,rows", [(2, 32), (3, 64), (4, 0), (4, 8), (4, 37), (4, 64), (4, 256)])
+@pytest.mark.parametrize("T,rows", [(2, 32), (3, 64), (4, 0), (4, 8), (4, 37), (4, 64), (4, 256), (6, 0), (6, 24),
+                                    (6, 64)])
 @pytest.mark.parametrize("shape", SIZES + [(5, 3), (121, 1), (1, 200)], ids=lambda s: f"{s[0]}x{s[1]}")
 def test_stream_equals_single_steps_bitwise(w, scheme, bc, T, rows, shape):
     """The register-streaming kernel: strips of 128 columns (one warp) and
-    32..256 rows, grids from a single row or column to several strips each
-    way with ragged edges."""
+    8..256 rows, depths 2..6, grids from a single row or column to several
+    strips each way with ragged edges."""
     nx, ny = shape
     u0, v0, h = smooth_ic(nx, ny, bc, seed=nx + ny + T + 1)
     lam = 0.9 * LAMBDA_MAX[scheme]
@@ -84,7 +85,7 @@ def test_stream_mode_switches_graphs_and_oracle(orc, w, bc):
     with w.Wave2D(n, n, h, lam * h, scheme=13, bc=bc, dtype=w.F32) as sim:
         sim.first_step(u0, v0)
         sim.set_tuning(kernel=w.KERNEL_STREAM, temporal_t=4, tile_h=64, use_graph=1)
-        sim.step_n(70)          # graph replays of 32 levels + 6 more
+        sim.step_n(70)          # a graph replay of 48 levels + 22 more
         assert sim.info().kernel == w.KERNEL_STREAM and sim.info().temporal_t == 4
         sim.set_tuning(kernel=w.KERNEL_TEMPORAL, temporal_t=4, use_graph=0)
         sim.step_n(21)
@@ -123,7 +124,7 @@ def test_mode_switches_and_graphs(w, bc):
         sim.set_tuning(kernel=w.KERNEL_TMA, use_graph=0)
         sim.step_n(21)
         sim.set_tuning(kernel=w.KERNEL_TEMPORAL, temporal_t=4, use_graph=1)
-        sim.step_n(70)          # two graph replays of 32 levels + 6 more
+        sim.step_n(70)          # a graph replay of 48 levels + 22 more
         sim.set_tuning(kernel=w.KERNEL_SIMPLE, use_graph=0)
         sim.step_n(9)
         sim.set_tuning(kernel=w.KERNEL_TEMPORAL, temporal_t=2, tile_h=32, use_graph=0)

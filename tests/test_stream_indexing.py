@@ -18,8 +18,14 @@ import pytest
 
 G = 16            # ghost ring width (kGhost)
 C = 4             # nodes per lane
-NB, PF = 8, 6     # ring slots per warp, rows copied ahead
 WARPS = 4         # warps per CTA
+DEPTHS = [2, 3, 4, 6]   # levels per launch the tuning accepts
+
+
+def ring_slots(scheme):
+    """Ring slots per warp and rows copied ahead (StreamCfg::NB, ::PF)."""
+    nb = 8 if scheme == 13 else 4
+    return nb, nb - 2
 
 
 def plane_geometry(nx, ny):
@@ -36,6 +42,7 @@ def stream_row(y, ny, ymax, wrap):
 
 def replay(nx, ny, scheme, T, L, periodic=False):
     R = 2 if scheme == 13 else 1
+    NB, PF = ring_slots(scheme)
     HX = (R * T + 3) // 4 * 4
     W = 32 * C
     OW = W - 2 * HX
@@ -47,7 +54,7 @@ def replay(nx, ny, scheme, T, L, periodic=False):
     def off(i, j):
         return (j + G) * pitch + (i + G)
 
-    wrap = periodic and scheme != 13 and nx % 4 == 0 and ny >= 16   # the launcher's condition
+    wrap = periodic and nx % 4 == 0 and ny >= 16   # the launcher's condition
     covered = {}
     for strip in range(strips_x * strips_y):
         warp = strip % WARPS
@@ -91,7 +98,7 @@ SHAPES = [(1, 1), (5, 3), (13, 31), (64, 64), (121, 1), (1, 200), (120, 17), (30
 
 
 @pytest.mark.parametrize("scheme", [5, 9, 13])
-@pytest.mark.parametrize("T", [2, 3, 4])
+@pytest.mark.parametrize("T", DEPTHS)
 @pytest.mark.parametrize("L", [8, 16, 37, 64])
 @pytest.mark.parametrize("periodic", [False, True], ids=["clamped", "periodic"])
 def test_loads_in_bounds_and_stores_cover_each_node_once(scheme, T, L, periodic):
@@ -103,10 +110,12 @@ def test_halo_reaches_every_dependency():
     """A node stored at level T depends on level-0 nodes up to R T rows and
     columns away; the strip's halo columns and warm-up rows must hold all of
     them (else a stored node would read a halo lane's unfinished value)."""
-    for scheme, T in itertools.product((5, 9, 13), (2, 3, 4)):
+    for scheme, T in itertools.product((5, 9, 13), DEPTHS):
         R = 2 if scheme == 13 else 1
         HX = (R * T + 3) // 4 * 4
-        assert HX >= R * T and HX <= G and R * (T + 1) <= G
+        assert HX >= R * T and HX <= G and R * (T + 1) < G
+        NB, PF = ring_slots(scheme)
+        assert PF + 2 <= NB   # a slot is refilled two steps after its last read
 
 
 def wrap(i, n):

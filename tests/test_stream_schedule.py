@@ -67,7 +67,7 @@ def replay_strip(R, T, L, y0=0):
 
 
 @pytest.mark.parametrize("R", [1, 2])
-@pytest.mark.parametrize("T", [2, 3, 4])
+@pytest.mark.parametrize("T", [2, 3, 4, 6])
 @pytest.mark.parametrize("L", [8, 9, 16, 17, 37, 48, 64])
 def test_ring_schedule(R, T, L):
     replay_strip(R, T, L)
@@ -78,7 +78,7 @@ def test_first_valid_rows_are_the_halo_bound():
     """Level t is valid from row rho0 + t R: the R T rows of input above the
     strip (and below it, by symmetry of the window) are exactly enough."""
     for R in (1, 2):
-        for T in (2, 3, 4):
+        for T in (2, 3, 4, 6):
             D, rho0 = R, -R * T
             for t in range(1, T + 1):
                 first_step = t * (D + R)
