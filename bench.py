@@ -56,13 +56,10 @@ KSHORT = {1: "simple", 2: "tma", 3: "temporal", 4: "stream"}
 # DRAM bytes (read + write) of one launch of a kernel at the benchmark size,
 # from an ncu capture of the same kernel source (see the profiles directory),
 # keyed by (kernel, hash of that kernel's sources without comments, scheme,
-# rows per tile or strip) so that a figure is dropped once the kernel or the
-# autotuner's choice changes.
-NCU_TRAFFIC = {("k5_stream", "c86b8d74b86b257b", 9, 16): 171168256 + 92256512,
-               ("k5_stream", "c86b8d74b86b257b", 9, 48): 176076544 + 91702784,
-               ("k5_stream", "c86b8d74b86b257b", 13, 32): 194497280 + 92939520,
-               ("k5_stream", "c86b8d74b86b257b", 13, 48): 192406528 + 92010752,
-               ("k2_tma", "13f358cdeaa5c663", 13, 0): 135366144 + 19828224}
+# rows per tile or strip, levels per launch) so that a figure is dropped once
+# the kernel or the autotuner's choice changes.
+NCU_TRAFFIC = {("k5_stream", "16a0978c41d1cf0c", 9, 64, 6): 165027072 + 92544000,
+               ("k5_stream", "16a0978c41d1cf0c", 13, 64, 4): 181718528 + 92793344}
 
 # Sources each kernel is built from (the hash keys of NCU_TRAFFIC).
 KERNEL_SOURCES = {"k2_tma": ("kernels.cuh", "stencil_ops.cuh"),
@@ -401,7 +398,16 @@ def run_ours(args, rank, world, local_rank):
     clocks = clk.summary()
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     mhz = clocks.get("sm_max_mhz") or 2070.0
-    alu_peak = sms * 128 * mhz * 1e6 / 1e12
+    spec_alu = sms * 128 * mhz * 1e6 / 1e12
+    # The FP32-pipe peak measured on this GPU (wave2d_alu_peaks: the best of
+    # scalar FMA, packed f32x2 FMA and add throughput), the denominator of the
+    # temporal kernels' ALU roofline; the spec figure rides along.
+    pk = w.alu_peaks(stream.cuda_stream)
+    alu_peak = max(pk.fp32_fma, pk.fp32_fma2, pk.fp32_add) / 1e12
+    alu_measured = {"fp32_fma_tops": round(pk.fp32_fma / 1e12, 3), "fp32_fma2_tops": round(pk.fp32_fma2 / 1e12, 3),
+                    "fp32_add_tops": round(pk.fp32_add / 1e12, 3), "fp64_fma_tops": round(pk.fp64_fma / 1e12, 4),
+                    "unit": "T lane operations/s (FMA = 1)", "spec_fp32_tops": round(spec_alu, 2),
+                    "spec": f"{sms} SMs x 128 FP32 lanes x {mhz:.0f} MHz"}
     # One roofline per kernel in step_n, over the launches of the schemes that
     # use it.  step_n(1999) of a multi-level kernel = floor(1999 / T) launches
     # of T levels + (1999 mod T) one-step launches (timed separately above).
@@ -420,7 +426,7 @@ def run_ours(args, rank, world, local_rank):
         avg_launch = total / n_launch
         alg_bytes = (16 if T > 1 else 12) * N * N  # read the two levels, write two (one for one step)
         achieved = alg_bytes / avg_launch / 1e9
-        per = [NCU_TRAFFIC.get((kname, kernel_source_hash(kname), s, tuned[s]["tile_h"] if T > 1 else 0))
+        per = [NCU_TRAFFIC.get((kname, kernel_source_hash(kname), s, tuned[s]["tile_h"] if T > 1 else 0, T))
                for s in ss]
         traffic = int(sum(per) / len(per)) if all(per) else None  # mean over the schemes' launches
         label = f"{kname} (FP32, T={T}, {'/'.join(str(s) for s in ss)}-point)"
@@ -443,7 +449,9 @@ def run_ours(args, rank, world, local_rank):
         rooflines.append({"bound": "alu", "kernel": label, "achieved": round(alu, 2), "peak": round(alu_peak, 2),
                           "unit": "TFLOP/s", "frac": round(alu / alu_peak, 4),
                           "flop": "one FP32 add, multiply or fused multiply-add (one FP32-pipe lane slot)",
-                          "peak_source": f"{sms} SMs x 128 FP32 lanes x {mhz:.0f} MHz (maximum SM clock)",
+                          "peak_source": "measured on this GPU (wave2d_alu_peaks: best of scalar FMA, packed "
+                                         "f32x2 FMA and add lane-operation rates)",
+                          "frac_of_spec": round(alu / spec_alu, 4),
                           "algorithmic_flop_per_launch": int(alg_ops), "levels_per_launch": T,
                           "avg_launch_us": round(avg_launch * 1e6, 3), "traffic": traffic,
                           "share_of_step_n": hbm_view["share_of_step_n"], "hbm": hbm_view})
@@ -471,9 +479,10 @@ def run_ours(args, rank, world, local_rank):
         "one_step_kernel": ({"kernel": "k2_tma", "avg_launch_us": {str(s): round(one_step[s] * 1e6, 3) for s in SCHEMES},
                              "frac": {str(s): round(12 * N * N / one_step[s] / 1e9 / peak, 4) for s in SCHEMES},
                              "algorithmic_bytes_per_launch": 12 * N * N,
-                             "traffic": NCU_TRAFFIC.get(("k2_tma", kernel_source_hash("k2_tma"), 13, 0))}
+                             "traffic": NCU_TRAFFIC.get(("k2_tma", kernel_source_hash("k2_tma"), 13, 0, 1))}
                             if all(one_step[s] for s in SCHEMES) else None),
         "clocks": clocks,
+        "alu_peaks_measured": alu_measured,
         "result_norms": {str(s): [results[s][0], results[s][1]] for s in SCHEMES},
     }
     if world == 1 and not args.no_extras:

@@ -503,6 +503,25 @@ int64_t wave2d_launch_count(void);
 /* Stability limit of a scheme (conventional = 1 for the comparison scheme). */
 double wave2d_lambda_max(int scheme, int conventional);
 
+/* Arithmetic throughput of the current device, measured: the denominators of
+ * the ALU rooflines of this library's kernels (the paper has no counterpart;
+ * it is a measurement service).  Every field except sms and clock_khz is in
+ * lane operations per second, one lane operation being one add or one fused
+ * multiply-add of one lane (a packed f32x2 FMA counts two): many independent
+ * chains per thread, 4 blocks of 512 threads per SM, best of 5 timed
+ * launches after 3 warm-ups (CUDA events on `stream`, NULL = default
+ * stream; the call synchronises it).  Allocates a small scratch buffer
+ * through the allocator hook for the duration of the call. */
+typedef struct {
+    double fp32_fma;   /* scalar FP32 fused multiply-add                    */
+    double fp32_fma2;  /* packed fma.rn.f32x2 (the temporal kernels' form)  */
+    double fp32_add;   /* scalar FP32 add                                   */
+    double fp64_fma;   /* FP64 fused multiply-add                           */
+    int32_t sms;       /* streaming multiprocessors                         */
+    int32_t clock_khz; /* the device's maximum SM clock attribute           */
+} wave2d_alu_peaks_t;
+int wave2d_alu_peaks(wave2d_alu_peaks_t *out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

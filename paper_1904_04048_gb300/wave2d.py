@@ -100,6 +100,11 @@ class wave2d_server_stats_t(ctypes.Structure):
                 ("max_resident_seen", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
+class wave2d_alu_peaks_t(ctypes.Structure):
+    _fields_ = [("fp32_fma", ctypes.c_double), ("fp32_fma2", ctypes.c_double), ("fp32_add", ctypes.c_double),
+                ("fp64_fma", ctypes.c_double), ("sms", ctypes.c_int32), ("clock_khz", ctypes.c_int32)]
+
+
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 
@@ -134,6 +139,7 @@ SIGNATURES = {
     "wave2d_last_error": (ctypes.c_char_p, []),
     "wave2d_launch_count": (ctypes.c_int64, []),
     "wave2d_lambda_max": (ctypes.c_double, [ctypes.c_int, ctypes.c_int]),
+    "wave2d_alu_peaks": (ctypes.c_int, [ctypes.POINTER(wave2d_alu_peaks_t), _P]),
     "wave2d_batch_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.POINTER(wave2d_tune),
                                            ctypes.POINTER(_P)]),
     "wave2d_batch_first_step": (ctypes.c_int, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.c_int]),
@@ -191,6 +197,14 @@ def launch_count() -> int:
 
 def lambda_max(scheme: int, conventional: bool = False) -> float:
     return lib().wave2d_lambda_max(scheme, int(conventional))
+
+
+def alu_peaks(stream=None) -> wave2d_alu_peaks_t:
+    """wave2d_alu_peaks: measured FP32 / FP64 lane operations per second of
+    the current device (``stream``: a cudaStream_t as int, or None)."""
+    out = wave2d_alu_peaks_t()
+    check(lib().wave2d_alu_peaks(ctypes.byref(out), stream))
+    return out
 
 
 def derive_scheme(m: int) -> wave2d_scheme:

@@ -218,3 +218,15 @@ def test_stream_tuning_is_validated(w):
     with w.Wave2D(n, n, 1.0 / n, 0.5 / n, scheme=9, bc=BC_PERIODIC, dtype=w.F64) as sim:
         sim.set_tuning(kernel=w.KERNEL_STREAM)   # FP64: falls back to a one-level kernel
         assert sim.info().kernel in (w.KERNEL_TMA, w.KERNEL_SIMPLE)
+
+
+def test_alu_peaks_are_measured_rates(w):
+    """wave2d_alu_peaks: FP32 lane-operation rates within [0.5, 1.2] of the
+    device's 128 FP32 lanes per SM at its clock attribute, and FP64 well
+    below FP32 (GB300's FP64 rate is a small fraction of its FP32 rate)."""
+    p = w.alu_peaks()
+    assert p.sms > 0 and p.clock_khz > 0
+    spec = p.sms * 128 * p.clock_khz * 1e3
+    for v in (p.fp32_fma, p.fp32_fma2, p.fp32_add):
+        assert 0.5 * spec < v < 1.2 * spec, (v, spec)
+    assert 0 < p.fp64_fma < 0.5 * p.fp32_fma
