@@ -59,7 +59,8 @@ KSHORT = {1: "simple", 2: "tma", 3: "temporal", 4: "stream"}
 # rows per tile or strip, levels per launch) so that a figure is dropped once
 # the kernel or the autotuner's choice changes.
 NCU_TRAFFIC = {("k5_stream", "16a0978c41d1cf0c", 9, 64, 6): 165027072 + 92544000,
-               ("k5_stream", "16a0978c41d1cf0c", 13, 64, 4): 181718528 + 92793344}
+               ("k5_stream", "16a0978c41d1cf0c", 13, 64, 4): 181718528 + 92793344,
+               ("k2_tma", "401b0f6d524d25c7", 13, 0, 1): 135363840 + 19898368}
 
 # Sources each kernel is built from (the hash keys of NCU_TRAFFIC).
 KERNEL_SOURCES = {"k2_tma": ("kernels.cuh", "stencil_ops.cuh"),

@@ -339,6 +339,38 @@ int wave2d_autotune(wave2d_t h, int64_t steps, wave2d_tune *best);
 int wave2d_get_info(wave2d_t h, wave2d_info_t *info);
 int wave2d_sync(wave2d_t h);
 
+/* Row access for domain decomposition.  Eq. A2 updates a node from the
+ * nodes within the stencil radius R of it (Section 4, the stencil Q_m around
+ * node (i, j)), so a band of rows advanced T levels stays exact R T rows in
+ * from its edges: a partition of the grid into row slabs, each extended by
+ * R T halo rows and refreshed from its neighbours every T levels, reproduces
+ * the undivided run bit for bit.  These calls move the halo rows.
+ *   get_rows: copy rows [j0, j0 + nrows) of the two state planes of h to
+ *             prev (u^{k-1}; d^k for WAVE2D_DIFF_FORM) and cur (u^k), each a
+ *             packed block of nrows * nx values of the storage type (F64:
+ *             double; F32: float; F32X2: nrows * nx hi floats followed by
+ *             nrows * nx lo floats), row r of the block at r * nx.
+ *   set_rows: the reverse; the ghost-ring images (periodic, odd) of h are
+ *             rewritten afterwards.
+ * on_device = 1: prev / cur are device memory and the copies are queued on
+ * the handle's stream (synchronise it before other streams use the buffer);
+ * 0: host memory, the call returns when the copy is done.  The caller owns
+ * the buffers.  WAVE2D_ERR_ARG for rows outside 0 .. ny or a null buffer,
+ * WAVE2D_ERR_STATE before the first step. */
+int wave2d_get_rows(wave2d_t h, int j0, int nrows, void *prev, void *cur, int on_device);
+int wave2d_set_rows(wave2d_t h, int j0, int nrows, const void *prev, const void *cur, int on_device);
+
+/* The unnormalised terms of the error norms (wave2d_error_vs_exact) over rows
+ * [j0, j0 + nrows) of u^k, with the exact solution evaluated as if local row
+ * j were row j + row_shift of a larger grid (a slab's offset in the whole
+ * grid): sums[0] = sum (u - u_e)^2, sums[1] = sum u_e^2, sums[2] =
+ * max |u - u_e|, sums[3] = max |u_e|, reduced in FP64 on the device.  Slabs
+ * combine them by a sum (0, 1) and a maximum (2, 3) into the norms of
+ * Eq. error.  Synchronises the stream; WAVE2D_ERR_NONFINITE if the rows hold
+ * NaN or Inf. */
+int wave2d_error_sums(wave2d_t h, const wave2d_exact *ex, int j0, int nrows, int64_t row_shift,
+                      double *sums);
+
 /* Failure-detection self-test: launch, on the handle's stream, a kernel that
  * waits on an mbarrier nothing ever completes, through the same bounded wait
  * every pipelined kernel uses, with a limit of limit_cycles SM clocks

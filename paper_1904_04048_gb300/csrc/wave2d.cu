@@ -1207,6 +1207,121 @@ int wave2d_set_raw(wave2d_t h, const void* src, int64_t bytes, int64_t k) {
     return refresh_ghosts(h);  // the copied rings may come from a shallower mode
 }
 
+// Rows [j0, j0 + nrows) of the two state planes, in the storage type, to or
+// from a packed buffer of nrows * nx values per plane (two such blocks, hi
+// then lo, for F32X2).  Plane order as in the raw layout: u^{k-1} (d^k for the
+// difference form), then u^k.
+static int copy_rows(wave2d* h, int j0, int nrows, void* prev, void* cur, const void* cprev, const void* ccur,
+                     int on_device, bool to_handle) {
+    if (!h) return set_error(WAVE2D_ERR_ARG, "null handle");
+    if (!h->initialized) return set_error(WAVE2D_ERR_STATE, "no state yet");
+    if (j0 < 0 || nrows < 0 || j0 + (int64_t)nrows > h->ny)
+        return set_error(WAVE2D_ERR_ARG, "rows [%d, %d) outside 0 .. %d", j0, j0 + nrows, h->ny);
+    if (nrows == 0) return WAVE2D_OK;
+    const size_t el = h->elem, rowb = (size_t)h->nx * el, block = rowb * nrows;
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice
+                                          : (to_handle ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToHost);
+    const int planes[2] = {h->diff_form ? 2 : h->prv, h->cur};
+    for (int q = 0; q < 2; ++q) {
+        char* ext = static_cast<char*>(to_handle ? const_cast<void*>(q ? ccur : cprev) : (q ? cur : prev));
+        if (!ext) return set_error(WAVE2D_ERR_ARG, "null row buffer");
+        for (int part = 0; part < (h->lo[0] ? 2 : 1); ++part) {
+            char* base = static_cast<char*>(part ? h->lo[planes[q]] : h->hi[planes[q]]);
+            char* pl = base + ((size_t)(j0 + h->G) * h->pitch + h->G) * el;
+            char* buf = ext + part * block;
+            const cudaError_t e = to_handle
+                ? cudaMemcpy2DAsync(pl, (size_t)h->pitch * el, buf, rowb, rowb, nrows, kind, h->stream)
+                : cudaMemcpy2DAsync(buf, rowb, pl, (size_t)h->pitch * el, rowb, nrows, kind, h->stream);
+            if (e != cudaSuccess) return cuda_fail(e, "row copy");
+        }
+    }
+    if (to_handle) {
+        // periodic / odd images in the ghost ring follow the new rows
+        h->rings_stale = false;
+        int rc = refresh_ghosts(h);
+        if (rc != WAVE2D_OK) return rc;
+    }
+    if (!on_device) W2D_CUDA(cudaStreamSynchronize(h->stream), "stream synchronize");
+    return WAVE2D_OK;
+}
+
+int wave2d_get_rows(wave2d_t h, int j0, int nrows, void* prev, void* cur, int on_device) {
+    NvtxRange nvtx_range("wave2d_get_rows");
+    return copy_rows(h, j0, nrows, prev, cur, nullptr, nullptr, on_device, false);
+}
+
+int wave2d_set_rows(wave2d_t h, int j0, int nrows, const void* prev, const void* cur, int on_device) {
+    NvtxRange nvtx_range("wave2d_set_rows");
+    return copy_rows(h, j0, nrows, nullptr, nullptr, prev, cur, on_device, true);
+}
+
+int wave2d_error_sums(wave2d_t h, const wave2d_exact* ex, int j0, int nrows, int64_t row_shift, double* sums) {
+    NvtxRange nvtx_range("wave2d_error_sums");
+    if (!h || !sums) return set_error(WAVE2D_ERR_ARG, "null argument");
+    if (!h->initialized) return set_error(WAVE2D_ERR_STATE, "no time level computed yet");
+    if (j0 < 0 || nrows < 1 || j0 + (int64_t)nrows > h->ny)
+        return set_error(WAVE2D_ERR_ARG, "rows [%d, %d) outside 0 .. %d", j0, j0 + nrows, h->ny);
+    wave2d_exact none{};
+    if (!ex) ex = &none;
+    if (!valid_exact(ex)) return set_error(WAVE2D_ERR_ARG, "invalid exact-solution description");
+    // tables of the exact solution: P, R over the nx columns, Q, S over the
+    // rows j0 .. j0 + nrows - 1 placed at global rows j + row_shift
+    std::vector<double> tab(2 * (size_t)h->nx + 2 * (size_t)nrows, 0.0);
+    double* P = tab.data();
+    double* R = P + h->nx;
+    double* Q = R + h->nx;
+    double* S = Q + nrows;
+    const double pi = 3.14159265358979323846;
+    for (int i = 0; i < h->nx; ++i) {
+        const double x = (i + ex->x_off) * h->h;
+        if (ex->kind == WAVE2D_EXACT_STANDING) P[i] = std::sin(2.0 * pi * ex->m * x);
+        else if (ex->kind == WAVE2D_EXACT_PLANE) {
+            P[i] = std::cos(ex->k1 * x);
+            R[i] = std::sin(ex->k1 * x);
+        }
+    }
+    for (int j = 0; j < nrows; ++j) {
+        const double y = ((double)(j0 + j + row_shift) + ex->x_off) * h->h;
+        if (ex->kind == WAVE2D_EXACT_STANDING) Q[j] = std::sin(2.0 * pi * ex->m * y);
+        else if (ex->kind == WAVE2D_EXACT_PLANE) {
+            Q[j] = std::cos(ex->k2 * y);
+            S[j] = std::sin(ex->k2 * y);
+        }
+    }
+    if (ex->kind != WAVE2D_EXACT_NONE)
+        W2D_CUDA(cudaMemcpyAsync(h->tab_eval, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice,
+                                 h->stream),
+                 "exact table upload");
+    ExactTab et{};
+    et.kind = ex->kind;
+    et.P = h->tab_eval;
+    et.R = h->tab_eval + h->nx;
+    et.Q = h->tab_eval + 2 * (size_t)h->nx;
+    et.S = h->tab_eval + 2 * (size_t)h->nx + nrows;
+    exact_weights(h, *ex, (double)h->k * h->tau, et.w0, et.w1);
+    const Reduce rd = make_reduce(h, h->acc_eval, 0);
+    // the rows as a grid of their own: the level planes shifted by j0 rows
+    Level L = h->level(h->cur);
+    const size_t shift = (size_t)j0 * h->pitch * h->elem;
+    L.hi = static_cast<char*>(L.hi) + shift;
+    if (L.lo) L.lo = static_cast<char*>(L.lo) + shift;
+    const Geo g{h->nx, nrows, h->pitch, h->G};
+    const int gx = std::min((h->nx + 255) / 256, 16);
+    const dim3 grd(gx, std::max(1, std::min(nrows, 8 * h->num_sms / gx)));
+    dispatch_dt(h->dtype, [&](auto DTc) {
+        k4_norms<decltype(DTc)::value><<<grd, 256, 0, h->stream>>>(L, g, et, rd);
+    });
+    W2D_LAUNCHED("norm kernel launch");
+    int st = 0;
+    W2D_CUDA(cudaMemcpyAsync(sums, h->acc_eval, 4 * sizeof(double), cudaMemcpyDeviceToHost, h->stream), "norm copy");
+    W2D_CUDA(cudaMemcpyAsync(&st, h->status, sizeof st, cudaMemcpyDeviceToHost, h->stream), "status copy");
+    W2D_CUDA(cudaStreamSynchronize(h->stream), "stream synchronize");
+    if (st) cudaMemsetAsync(h->status, 0, sizeof(int), h->stream);
+    if (st & STATUS_TIMEOUT) return set_error(WAVE2D_ERR_TIMEOUT, "a device-side wait exceeded its limit");
+    if (st & STATUS_NONFINITE) return set_error(WAVE2D_ERR_NONFINITE, "the field contains NaN or Inf");
+    return WAVE2D_OK;
+}
+
 int wave2d_autotune(wave2d_t h, int64_t steps, wave2d_tune* best) {
     NvtxRange nvtx_range("wave2d_autotune");
     if (!h) return set_error(WAVE2D_ERR_ARG, "null handle");

@@ -140,6 +140,10 @@ SIGNATURES = {
     "wave2d_launch_count": (ctypes.c_int64, []),
     "wave2d_lambda_max": (ctypes.c_double, [ctypes.c_int, ctypes.c_int]),
     "wave2d_alu_peaks": (ctypes.c_int, [ctypes.POINTER(wave2d_alu_peaks_t), _P]),
+    "wave2d_get_rows": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P, _P, ctypes.c_int]),
+    "wave2d_set_rows": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P, _P, ctypes.c_int]),
+    "wave2d_error_sums": (ctypes.c_int, [_P, ctypes.POINTER(wave2d_exact), ctypes.c_int, ctypes.c_int,
+                                         ctypes.c_int64, _D]),
     "wave2d_batch_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.POINTER(wave2d_tune),
                                            ctypes.POINTER(_P)]),
     "wave2d_batch_first_step": (ctypes.c_int, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.c_int]),
@@ -287,6 +291,20 @@ def _ptr(a):
     raise TypeError(type(a))
 
 
+def _buf_ptr(a):
+    """(pointer, on_device) of a contiguous numpy array or torch tensor."""
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("row buffers must be contiguous")
+        return a.ctypes.data_as(ctypes.c_void_p), 0
+    import torch
+    if isinstance(a, torch.Tensor):
+        if not a.is_contiguous():
+            raise ValueError("row buffers must be contiguous")
+        return ctypes.c_void_p(a.data_ptr()), int(a.is_cuda)
+    raise TypeError(type(a))
+
+
 class Wave2D:
     """One simulation handle (``wave2d_t``)."""
 
@@ -363,6 +381,42 @@ class Wave2D:
         check(lib().wave2d_set_state(self._h, up.ctypes.data_as(ctypes.c_void_p),
                                      uc.ctypes.data_as(ctypes.c_void_p), int(k), 0))
 
+    def row_block_shape(self, nrows):
+        """Shape and numpy dtype of one plane's packed row block of
+        wave2d_get_rows / wave2d_set_rows for this handle's storage type."""
+        dt = self.info().dtype
+        if dt == F64:
+            return (nrows, self.nx), np.float64
+        if dt == F32X2:
+            return (2, nrows, self.nx), np.float32
+        return (nrows, self.nx), np.float32
+
+    def get_rows(self, j0, nrows, prev, cur):
+        """wave2d_get_rows into caller buffers of ``row_block_shape(nrows)``:
+        numpy arrays (host) or contiguous CUDA tensors (device, queued on the
+        handle's stream)."""
+        pp, dp = _buf_ptr(prev)
+        pc, dc = _buf_ptr(cur)
+        if dp != dc:
+            raise ValueError("prev and cur must both be on the host or both on the device")
+        check(lib().wave2d_get_rows(self._h, int(j0), int(nrows), pp, pc, dp))
+
+    def set_rows(self, j0, nrows, prev, cur):
+        """wave2d_set_rows from buffers of ``row_block_shape(nrows)``."""
+        pp, dp = _buf_ptr(prev)
+        pc, dc = _buf_ptr(cur)
+        if dp != dc:
+            raise ValueError("prev and cur must both be on the host or both on the device")
+        check(lib().wave2d_set_rows(self._h, int(j0), int(nrows), pp, pc, dp))
+
+    def error_sums(self, ex, j0, nrows, row_shift=0):
+        """wave2d_error_sums: [sum (u-u_e)^2, sum u_e^2, max |u-u_e|, max |u_e|]
+        over rows j0 .. j0 + nrows - 1, u_e placed at rows + row_shift."""
+        out = (ctypes.c_double * 4)()
+        check(lib().wave2d_error_sums(self._h, ctypes.byref(ex) if ex is not None else None, int(j0), int(nrows),
+                                      int(row_shift), out))
+        return [out[0], out[1], out[2], out[3]]
+
     def get_raw(self):
         nb = check(lib().wave2d_raw_bytes(self._h))
         buf = np.empty(nb, dtype=np.uint8)
@@ -378,7 +432,8 @@ class Wave2D:
         """wave2d_set_tuning: ``kernel`` one of KERNEL_AUTO / SIMPLE / TMA /
         TEMPORAL / STREAM; ``tile_h`` rows per tile (TEMPORAL: 16, 24, 32, 64)
         or per strip (STREAM: 8 .. 4096), 0 = default; ``temporal_t`` levels
-        per launch of the two multi-level kernels (2, 3, 4; 0 = 4)."""
+        per launch of the two multi-level kernels (TEMPORAL: 2, 3, 4; STREAM:
+        2, 3, 4, 6; 0 = the default depth)."""
         t = wave2d_tune(int(kernel), int(tile_h), int(temporal_t), int(use_graph), int(ctas_per_sm))
         check(lib().wave2d_set_tuning(self._h, ctypes.byref(t)))
 

@@ -1,0 +1,116 @@
+"""Row-slab domain decomposition with the CUDA handles as local solvers:
+the slabs of one grid, each a wave2d handle of its owned and halo rows, held
+on one GPU and exchanging halo rows every T levels through
+wave2d_get_rows / wave2d_set_rows, end bit for bit where the undivided
+handle ends (Eq. A2 reads only the R-neighbourhood of a node, and every
+kernel evaluates a node identically); the combined norms
+(wave2d_error_sums over the owned rows) equal the undivided norms."""
+import math
+
+import numpy as np
+import pytest
+
+from initial_data import BC_PERIODIC, BC_ZERO, LAMBDA_MAX
+
+pytestmark = pytest.mark.gpu
+
+RADIUS = {5: 1, 9: 1, 13: 2}
+
+
+@pytest.fixture(scope="module")
+def w():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1904_04048_gb300 import build
+    build.build()
+    from paper_1904_04048_gb300 import wave2d
+    return wave2d
+
+
+def _ic(nx, ny, bc, seed):
+    rng = np.random.default_rng(seed)
+    h = 1.0 / nx
+    x, y = np.arange(nx) * h, np.arange(ny) * h
+    k1, k2 = 2 * math.pi * 3, 2 * math.pi * 2
+    u0 = np.cos(k1 * x[None, :] + k2 * y[:, None]) + 0.02 * rng.standard_normal((ny, nx))
+    v0 = 0.5 * rng.standard_normal((ny, nx))
+    if bc == BC_ZERO:
+        u0[:2] = u0[-2:] = 0.0
+    return u0, v0, h, (k1, k2)
+
+
+@pytest.mark.parametrize("scheme", [9, 13])
+@pytest.mark.parametrize("bc", [BC_ZERO, BC_PERIODIC], ids=["zero", "periodic"])
+@pytest.mark.parametrize("dtype", [0, 1, 2], ids=["f64", "f32", "f32x2"])
+@pytest.mark.parametrize("world,T,kernel", [(2, 4, "stream"), (3, 6, "auto"), (4, 3, "tma")])
+def test_slabs_on_one_gpu_equal_the_undivided_handle(w, scheme, bc, dtype, world, T, kernel):
+    import torch
+    from paper_1904_04048_gb300 import slab
+    nx, ny, n_t = 200, 131, 40
+    if scheme == 13 and T == 6 and kernel == "stream":
+        pytest.skip("depth 6 is not a streaming choice for 13 points here")
+    u0, v0, h, kk = _ic(nx, ny, bc, seed=scheme * 10 + world)
+    lam = 0.9 * LAMBDA_MAX[scheme]
+    tau = lam * h
+    tune = {"stream": dict(kernel=w.KERNEL_STREAM, temporal_t=4 if T % 4 == 0 else T, tile_h=32),
+            "tma": dict(kernel=w.KERNEL_TMA), "auto": dict()}[kernel]
+    if dtype != 1:
+        tune = {}  # the kernel choice applies to FP32 storage
+    with w.Wave2D(nx, ny, h, tau, scheme=scheme, bc=bc, dtype=dtype) as whole:
+        whole.set_tuning(**tune)
+        whole.first_step(u0, v0)
+        whole.step_n(n_t - 1)
+        rp, rc, _ = whole.get_state()
+        ex = w.exact(w.EXACT_PLANE, amp=1.0, k1=kk[0], k2=kk[1], x_off=0.0)
+        s_whole = whole.error_sums(ex, 0, ny, 0)
+    sims, runs = [], []
+    try:
+        for r in range(world):
+            plan = slab.plan_slabs(nx, ny, world, r, RADIUS[scheme], T, bc == BC_PERIODIC)
+            sim = w.Wave2D(nx, plan.ny_local, h, tau, scheme=scheme, bc=bc, dtype=dtype)
+            sims.append(sim)
+            sim.set_tuning(**tune)
+            runs.append(slab.SlabRun(plan, slab.HandleSolver(sim), device=torch.device("cuda")))
+        exch = slab.LocalExchange()
+        slab.first_step(runs, exch, [slab.extended_rows(r.plan, u0) for r in runs],
+                        [slab.extended_rows(r.plan, v0) for r in runs])
+        slab.step_n(runs, exch, n_t - 1)
+        gp, gc = [], []
+        for r, sim in zip(runs, sims):
+            up, uc, k = sim.get_state()
+            assert k == n_t
+            lo, hi = r.plan.owned_local
+            gp.append(up[lo:hi])
+            gc.append(uc[lo:hi])
+        assert np.array_equal(np.concatenate(gc), rc) and np.array_equal(np.concatenate(gp), rp)
+        l2, linf = slab.error_vs_exact(runs, exch, ex)
+        assert abs(l2 - math.sqrt(s_whole[0] / s_whole[1])) <= 1e-12 * l2
+        assert linf == s_whole[2] / s_whole[3]
+    finally:
+        for sim in sims:
+            sim.close()
+
+
+def test_row_access_round_trip_and_errors(w):
+    import torch
+    nx, ny = 37, 29
+    u0, v0, h, _ = _ic(nx, ny, BC_PERIODIC, seed=3)
+    with w.Wave2D(nx, ny, h, 0.5 * h, scheme=13, bc=BC_PERIODIC, dtype=2) as sim:
+        shape, dt = sim.row_block_shape(5)
+        with pytest.raises(w.Wave2DError):  # before the first step
+            sim.get_rows(0, 5, np.empty(shape, dt), np.empty(shape, dt))
+        sim.first_step(u0, v0)
+        sim.step_n(3)
+        a, b = np.empty(shape, dt), np.empty(shape, dt)
+        sim.get_rows(7, 5, a, b)
+        raw0, k0 = sim.get_raw()
+        ta, tb = torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda()
+        sim.set_rows(7, 5, ta, tb)          # device buffers: the same rows back
+        raw1, k1 = sim.get_raw()
+        assert k0 == k1 and np.array_equal(raw0, raw1)
+        for j0, n in ((-1, 2), (27, 3), (0, 30)):
+            with pytest.raises(w.Wave2DError) as e:
+                sim.get_rows(j0, n, np.empty(sim.row_block_shape(max(n, 1))[0], dt),
+                             np.empty(sim.row_block_shape(max(n, 1))[0], dt))
+            assert e.value.code == w.ERR_ARG
