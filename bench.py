@@ -385,6 +385,20 @@ def run_ours(args, rank, world, local_rank):
     barrier()
     e2e_elapsed = time.perf_counter() - t0
 
+    # Error of the benchmark's FP32 result (the last step's final level, k =
+    # 2000) against an FP64 run of the same inputs and levels on the GPU (the
+    # FP64 path matches the CPU oracle to 1e-12 in the parity tests).
+    result_error = {}
+    if not args.no_extras:
+        for s in SCHEMES:
+            lam = 0.9 * LAMBDA_MAX[s]
+            with w.Wave2D(N, N, h, lam * h, scheme=s, bc=BC_PERIODIC, dtype=w.F64,
+                          stream=stream.cuda_stream) as ref64:
+                ref64.first_step(du0, dv0)
+                ref64.step_n(STEPS_PER_SCHEME - 1)
+                l2, linf = sims[s].diff_norms(ref64)
+            result_error[str(s)] = {"rel_l2": l2, "rel_linf": linf}
+
     elapsed, e2e_elapsed = reduce_max([elapsed, e2e_elapsed], dev)
     pts_step = len(SCHEMES) * STEPS_PER_SCHEME * N * N
     value = whole_job_value(args.steps * pts_step, world, elapsed)
@@ -485,6 +499,9 @@ def run_ours(args, rank, world, local_rank):
         "clocks": clocks,
         "alu_peaks_measured": alu_measured,
         "result_norms": {str(s): [results[s][0], results[s][1]] for s in SCHEMES},
+        "result_error_vs_fp64": ({"reference": "FP64 run of the same inputs and levels on the GPU (the FP64 path "
+                                               "matches the CPU oracle to 1e-12 in the parity tests)",
+                                  **result_error} if result_error else None),
     }
     if world == 1 and not args.no_extras:
         line["fp64_5point_256"] = measure_small_fp64(w, torch)
@@ -492,6 +509,8 @@ def run_ours(args, rank, world, local_rank):
         line["served"] = measure_served(w, torch)
         line["derived_schemes"] = measure_derived(w, torch, u0, v0, peak)
         line["fp32_difference_sums"] = measure_diff_sums(w, torch, u0, v0, peak)
+        if args.precision != "off":
+            line["precision"] = measure_precision(w, torch, args.precision)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = time_oracle(u0, v0, args.cpu_budget)
         if not args.no_extras:
@@ -609,6 +628,112 @@ def measure_served(w, torch):
             "sequential_plain_value": round(seq, 2),
             "saturated_speedup_vs_sequential_plain": round(pts / wall_sat / 1e9 / seq, 2),
             "latency": "submission to norms on the host (library steady clock)"}
+
+
+PRECISION_SCOPES = {
+    "full": "N = 512..8192, schemes 5/9/13, modes (1,0), (3,4), (N/32,N/64); FP64, FP32, FP32 difference form, "
+            "FP32x2; FP64 the reference",
+    "bounded": "N <= 2048: schemes 5/9/13, modes (1,0), (3,4), (N/32,N/64), FP64/FP32/FP32 difference form/FP32x2, "
+               "FP64 the reference; 4096^2: every scheme and mode, FP32/difference form/FP32x2, FP32x2 the "
+               "reference; 8192^2: 9- and 13-point, modes (1,0) and (256,128), FP32/difference form/FP32x2, "
+               "FP32x2 the reference"}
+
+
+def precision_cases(scope: str):
+    """The plane-wave precision sweep: (N, scheme, (m1, m2), dtypes, reference).
+
+    Every case runs a periodic plane wave cos(k.x - c|k| t), k = 2 pi (m1, m2),
+    on the N^2 unit square, lambda = 0.9 of the scheme's limit, 10^4 two-steps
+    after the first step.  dtypes are "f64", "f32", "f32_diff_form" (FP32 with
+    WAVE2D_DIFF_FORM) and "f32x2"; the reference is the dtype the others are
+    compared with (FP64 where it runs; FP32x2, which tracks FP64 to ~1e-11,
+    above 2048^2, where an FP64 run of 10^4 levels takes 6-24 s per case).
+      full:    N = 512 .. 8192, schemes 5, 9, 13, modes (1,0), (3,4),
+               (N/32, N/64), all four dtypes, FP64 the reference.
+      bounded: N <= 2048 as full; 4096^2 every scheme and mode without FP64;
+               8192^2 the 9- and 13-point schemes, modes (1,0) and (N/32, N/64),
+               without FP64."""
+    out = []
+    for n in (512, 1024, 2048, 4096, 8192):
+        modes = [(1, 0), (3, 4), (n // 32, n // 64)]
+        schemes = (5, 9, 13)
+        if scope == "full" or n <= 2048:
+            dts, ref = ("f64", "f32", "f32_diff_form", "f32x2"), "f64"
+        else:
+            dts, ref = ("f32", "f32_diff_form", "f32x2"), "f32x2"
+            if n == 8192:
+                schemes, modes = (9, 13), [(1, 0), (n // 32, n // 64)]
+        for sc in schemes:
+            for m in modes:
+                out.append((n, sc, m, dts, ref))
+    return out
+
+
+def measure_precision(w, torch, scope: str, steps: int = 10000):
+    """Error of every storage mode over 10^4 steps of a periodic plane wave
+    (the precision sweep): relative L2 and L-infinity against the exact PDE
+    solution (FP64 norms on the device) and against the reference run of the
+    same case (wave2d_diff_norms), and the time per level (CUDA events around
+    step_n on the handle's stream)."""
+    import math
+    from initial_data import BC_PERIODIC, LAMBDA_MAX, plane_wave_ic
+    flags = {"f64": (w.F64, 0), "f32": (w.F32, 0), "f32_diff_form": (w.F32, w.DIFF_FORM), "f32x2": (w.F32X2, 0)}
+    rows = []
+    t_start = time.perf_counter()
+    ic_cache = {}
+    for n, sc, (m1, m2), dts, ref_dt in precision_cases(scope):
+        h = 1.0 / n
+        lam = 0.9 * LAMBDA_MAX[sc]
+        tau = lam * h
+        k1, k2 = 2 * math.pi * m1, 2 * math.pi * m2
+        key = (n, m1, m2)
+        if key not in ic_cache:
+            ic_cache.clear()
+            u0, v0 = plane_wave_ic(n, n, h, k1, k2, BC_PERIODIC)
+            ic_cache[key] = (torch.from_numpy(u0).cuda(), torch.from_numpy(v0).cuda())
+            del u0, v0
+        du0, dv0 = ic_cache[key]
+        ex = w.exact(w.EXACT_PLANE, amp=1.0, k1=k1, k2=k2, x_off=0.0)
+        stream = torch.cuda.Stream()
+        sims = {}
+        try:
+            for dt in [ref_dt] + [d for d in dts if d != ref_dt]:
+                dtype, fl = flags[dt]
+                sim = w.Wave2D(n, n, h, tau, scheme=sc, bc=BC_PERIODIC, dtype=dtype, flags=fl,
+                               stream=stream.cuda_stream)
+                sims[dt] = sim
+                sim.first_step(du0, dv0)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                sim.step_n(steps)
+                e1.record(stream)
+                l2, linf, _ = sim.error_vs_exact(ex)
+                row = {"N": n, "scheme": sc, "mode": [m1, m2], "dtype": dt,
+                       "us_per_level": round(e0.elapsed_time(e1) * 1e3 / steps, 3),
+                       "kernel": KSHORT.get(sim.info().kernel), "err_exact_l2": l2, "err_exact_linf": linf}
+                if dt != ref_dt:
+                    rl2, rlinf = sim.diff_norms(sims[ref_dt])
+                    row.update({"err_ref_l2": rl2, "err_ref_linf": rlinf, "ref": ref_dt})
+                    sim.close()
+                    del sims[dt]
+                rows.append(row)
+        finally:
+            for sim in sims.values():
+                sim.close()
+    ic_cache.clear()
+    summary = {}
+    for r in rows:
+        if "err_ref_l2" not in r:
+            continue
+        k = f"{r['N']}_{r['dtype']}"
+        cur = summary.setdefault(k, {"max_err_ref_l2": 0.0, "max_err_ref_linf": 0.0, "ref": r["ref"]})
+        cur["max_err_ref_l2"] = max(cur["max_err_ref_l2"], r["err_ref_l2"])
+        cur["max_err_ref_linf"] = max(cur["max_err_ref_linf"], r["err_ref_linf"])
+    return {"workload": "periodic plane waves cos(k.x - c|k|t), k = 2 pi (m1, m2), N^2 unit square, "
+                        "lambda = 0.9 lambda_max, 10^4 two-steps after the first step",
+            "scope": scope, "cases": PRECISION_SCOPES[scope],
+            "steps": steps, "seconds": round(time.perf_counter() - t_start, 1),
+            "max_error_vs_reference": summary, "rows": rows}
 
 
 def measure_small_fp64(w, torch):
@@ -792,6 +917,8 @@ def main():
     ap.add_argument("--fixed-tuning", action="store_true",
                     help="skip the autotuner (the kernels and rows of FIXED_TUNING, T = 4), e.g. under a profiler")
     ap.add_argument("--ref-levels", type=int, default=4, help="time levels per scheme per reference step")
+    ap.add_argument("--precision", choices=["off", "bounded", "full"], default="bounded",
+                    help="plane-wave precision sweep over storage modes (see precision_cases)")
     ap.add_argument("--profile-case", choices=["k2_tma", "k3_temporal", "k5_stream", "kc2_tma"],
                     help="run a short case of one kernel for a profiler capture and exit")
     ap.add_argument("--profile-scheme", type=int, choices=[5, 9, 13], default=13)

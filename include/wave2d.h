@@ -300,6 +300,16 @@ int wave2d_step_n(wave2d_t h, int64_t n);
 int wave2d_error_vs_exact(wave2d_t h, const wave2d_exact *ex, double *rel_l2, double *rel_linf,
                           double *spacetime_E);
 
+/* The current levels of two handles of the same grid size and level index k
+ * (any storage types, same device) compared in FP64 on the device:
+ *   rel_l2   = sqrt(sum (u_a - u_b)^2 / sum u_b^2)
+ *   rel_linf = max |u_a - u_b| / max |u_b|
+ * b is the reference (e.g. an FP64 run of the same problem: the error of a
+ * lower-precision run against it).  Orders a's stream after b's; synchronises
+ * a's stream.  WAVE2D_ERR_ARG for different sizes or devices,
+ * WAVE2D_ERR_STATE for different k. */
+int wave2d_diff_norms(wave2d_t a, wave2d_t b, double *rel_l2, double *rel_linf);
+
 /* Enable (ex != NULL) or disable (NULL) accumulation of the sums of Eq. error
  * after every step from the next first_step on.  Tracking uses the one-node-
  * per-thread kernel with the reduction fused into the step. */

@@ -437,6 +437,19 @@ __global__ void __launch_bounds__(256) k4_norms(Level L, Geo g, ExactTab ex, Red
     reduce_finalize<256>(s0, s1, m0, m1, rd);
 }
 
+// Norms of the difference of two fields of the same grid (any storage types),
+// relative to the second: the sums of k4_norms with b's value in place of the
+// exact solution.
+template <int DTA, int DTB>
+__global__ void __launch_bounds__(256) k_diff_norms(Level A, Geo ga, Level B, Geo gb, Reduce rd) {
+    double s0 = 0, s1 = 0, m0 = 0, m1 = 0;
+    for (int j = blockIdx.y; j < ga.ny; j += gridDim.y)
+        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ga.nx; i += gridDim.x * blockDim.x)
+            error_terms(St<DTA>::to_d(St<DTA>::ld(A, off(ga, i, j))), St<DTB>::to_d(St<DTB>::ld(B, off(gb, i, j))),
+                        s0, s1, m0, m1, rd.status);
+    reduce_finalize<256>(s0, s1, m0, m1, rd);
+}
+
 // ---------------------------------------------------------------------------
 // Plane <-> plain FP64 array.
 // ---------------------------------------------------------------------------

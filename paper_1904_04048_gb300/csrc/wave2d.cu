@@ -1322,6 +1322,42 @@ int wave2d_error_sums(wave2d_t h, const wave2d_exact* ex, int j0, int nrows, int
     return WAVE2D_OK;
 }
 
+int wave2d_diff_norms(wave2d_t a, wave2d_t b, double* rel_l2, double* rel_linf) {
+    NvtxRange nvtx_range("wave2d_diff_norms");
+    if (!a || !b) return set_error(WAVE2D_ERR_ARG, "null handle");
+    if (!a->initialized || !b->initialized) return set_error(WAVE2D_ERR_STATE, "no time level computed yet");
+    if (a->nx != b->nx || a->ny != b->ny) return set_error(WAVE2D_ERR_ARG, "the two grids differ in size");
+    if (a->device != b->device) return set_error(WAVE2D_ERR_ARG, "the two handles live on different devices");
+    if (a->k != b->k) return set_error(WAVE2D_ERR_STATE, "the two handles are at different levels");
+    // b's writes are ordered before a's stream reads them
+    cudaEvent_t ev = nullptr;
+    W2D_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "event create");
+    cudaEventRecord(ev, b->stream);
+    cudaStreamWaitEvent(a->stream, ev, 0);
+    cudaEventDestroy(ev);
+    const Reduce rd = make_reduce(a, a->acc_eval, 0);
+    const int gx = std::min((a->nx + 255) / 256, 16);
+    const dim3 grd(gx, std::max(1, std::min(a->ny, 8 * a->num_sms / gx)));
+    dispatch_dt(a->dtype, [&](auto DA) {
+        dispatch_dt(b->dtype, [&](auto DB) {
+            k_diff_norms<decltype(DA)::value, decltype(DB)::value><<<grd, 256, 0, a->stream>>>(
+                a->level(a->cur), a->geo(), b->level(b->cur), b->geo(), rd);
+        });
+    });
+    W2D_LAUNCHED("difference norm kernel launch");
+    double acc[4];
+    int st = 0;
+    W2D_CUDA(cudaMemcpyAsync(acc, a->acc_eval, sizeof acc, cudaMemcpyDeviceToHost, a->stream), "norm copy");
+    W2D_CUDA(cudaMemcpyAsync(&st, a->status, sizeof st, cudaMemcpyDeviceToHost, a->stream), "status copy");
+    W2D_CUDA(cudaStreamSynchronize(a->stream), "stream synchronize");
+    if (rel_l2) *rel_l2 = std::sqrt(acc[0] / acc[1]);
+    if (rel_linf) *rel_linf = acc[2] / acc[3];
+    if (st) cudaMemsetAsync(a->status, 0, sizeof(int), a->stream);
+    if (st & STATUS_TIMEOUT) return set_error(WAVE2D_ERR_TIMEOUT, "a device-side wait exceeded its limit");
+    if (st & STATUS_NONFINITE) return set_error(WAVE2D_ERR_NONFINITE, "the field contains NaN or Inf");
+    return WAVE2D_OK;
+}
+
 int wave2d_autotune(wave2d_t h, int64_t steps, wave2d_tune* best) {
     NvtxRange nvtx_range("wave2d_autotune");
     if (!h) return set_error(WAVE2D_ERR_ARG, "null handle");

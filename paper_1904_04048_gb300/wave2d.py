@@ -140,6 +140,7 @@ SIGNATURES = {
     "wave2d_launch_count": (ctypes.c_int64, []),
     "wave2d_lambda_max": (ctypes.c_double, [ctypes.c_int, ctypes.c_int]),
     "wave2d_alu_peaks": (ctypes.c_int, [ctypes.POINTER(wave2d_alu_peaks_t), _P]),
+    "wave2d_diff_norms": (ctypes.c_int, [_P, _P, _D, _D]),
     "wave2d_get_rows": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P, _P, ctypes.c_int]),
     "wave2d_set_rows": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P, _P, ctypes.c_int]),
     "wave2d_error_sums": (ctypes.c_int, [_P, ctypes.POINTER(wave2d_exact), ctypes.c_int, ctypes.c_int,
@@ -380,6 +381,13 @@ class Wave2D:
         up, uc = _host_f64(u_prev, n), _host_f64(u_cur, n)
         check(lib().wave2d_set_state(self._h, up.ctypes.data_as(ctypes.c_void_p),
                                      uc.ctypes.data_as(ctypes.c_void_p), int(k), 0))
+
+    def diff_norms(self, ref: "Wave2D"):
+        """wave2d_diff_norms: (relative L2, relative L-infinity) of this
+        handle's current level against ``ref``'s (same grid, same k)."""
+        l2, linf = ctypes.c_double(), ctypes.c_double()
+        check(lib().wave2d_diff_norms(self._h, ref.handle, ctypes.byref(l2), ctypes.byref(linf)))
+        return l2.value, linf.value
 
     def row_block_shape(self, nrows):
         """Shape and numpy dtype of one plane's packed row block of

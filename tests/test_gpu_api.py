@@ -230,3 +230,37 @@ def test_alu_peaks_are_measured_rates(w):
     for v in (p.fp32_fma, p.fp32_fma2, p.fp32_add):
         assert 0.5 * spec < v < 1.2 * spec, (v, spec)
     assert 0 < p.fp64_fma < 0.5 * p.fp32_fma
+
+
+def test_diff_norms_match_the_host_difference(w):
+    """wave2d_diff_norms: the FP64 norms of the difference of two handles'
+    current levels, relative to the second, equal the host computation from
+    the two states; mismatched sizes or levels are refused."""
+    import math as _m
+    n = 96
+    h = 1.0 / n
+    k1, k2 = 2 * _m.pi * 3, 2 * _m.pi * 1
+    from initial_data import plane_wave_ic
+    u0, v0 = plane_wave_ic(n, n, h, k1, k2, BC_PERIODIC)
+    with w.Wave2D(n, n, h, 0.5 * h, scheme=13, bc=BC_PERIODIC, dtype=w.F32) as a, \
+            w.Wave2D(n, n, h, 0.5 * h, scheme=13, bc=BC_PERIODIC, dtype=w.F64) as b, \
+            w.Wave2D(n, n + 1, h, 0.5 * h, scheme=13, bc=BC_PERIODIC, dtype=w.F64) as c:
+        for sim in (a, b):
+            sim.first_step(u0, v0)
+            sim.step_n(300)
+        l2, linf = a.diff_norms(b)
+        _, ua, _ = a.get_state()
+        _, ub, _ = b.get_state()
+        d = ua - ub
+        assert abs(l2 - np.linalg.norm(d) / np.linalg.norm(ub)) <= 1e-12 * l2
+        assert abs(linf - np.max(np.abs(d)) / np.max(np.abs(ub))) <= 1e-12 * linf
+        assert 1e-9 < l2 < 1e-4                       # FP32 rounding, not zero
+        assert b.diff_norms(b) == (0.0, 0.0)
+        with pytest.raises(w.Wave2DError) as e:       # different grid
+            c.first_step(np.zeros((n + 1, n)), np.zeros((n + 1, n)))
+            a.diff_norms(c)
+        assert e.value.code == w.ERR_ARG
+        a.step_n(1)
+        with pytest.raises(w.Wave2DError) as e:       # different level
+            a.diff_norms(b)
+        assert e.value.code == w.ERR_STATE
