@@ -439,12 +439,17 @@ int wave2d_error_norms_noalloc(const void *field, int dtype, int nx, int ny, int
 /* ------------------------------------------------------------------------ */
 typedef struct wave2d_batch *wave2d_batch_t;
 
-/* Group n handles; opt (may be NULL) fixes the quantum (temporal_t, 1..4)
- * and the tile height (tile_h, 32 or 64); zero fields keep the defaults
- * (4 and 32) until wave2d_batch_autotune chooses; use_graph = 0 launches the
- * quanta of every run directly (for runs used once) instead of capturing a
- * graph.  WAVE2D_ERR_ARG for
- * non-F32 handles, mixed boundaries or devices, or a repeated handle. */
+/* Group n handles; opt (may be NULL) chooses the kernel: 0 or
+ * WAVE2D_KERNEL_TEMPORAL for shared-memory regions (any boundary; tile_h 32
+ * or 64 rows), WAVE2D_KERNEL_STREAM for register streaming (zero boundary;
+ * one warp per strip of 8..1024 rows, tile_h, default 64, over the strips of
+ * all instances of a scheme, the three schemes as concurrent branches), and
+ * fixes the quantum (temporal_t, 1..4 levels per launch); zero fields keep
+ * the defaults (regions, 4 levels, 32 rows) until wave2d_batch_autotune
+ * chooses; use_graph = 0 launches the quanta of every run directly (for runs
+ * used once) instead of capturing a graph.  WAVE2D_ERR_ARG for non-F32
+ * handles, mixed boundaries or devices, a repeated handle, or streaming on a
+ * periodic batch. */
 int wave2d_batch_create(wave2d_t *handles, int n, const wave2d_tune *opt, wave2d_batch_t *out);
 
 /* First step (Eq. A1) of every instance in one launch: u0[i], v0[i] are the
@@ -458,9 +463,12 @@ int wave2d_batch_first_step(wave2d_batch_t b, const double *const *u0, const dou
  * handles' plane pairs repeat. */
 int wave2d_batch_run(wave2d_batch_t b, const int64_t *steps);
 
-/* Time the run for min(steps[i], probe_steps) levels with quanta 2 and 4 and
- * tile heights 32 and 64 on a snapshot of every instance, restore every
- * instance exactly and keep the fastest (written to *best, may be NULL). */
+/* Time the run for min(steps[i], probe_steps) levels with the candidate
+ * configurations on a snapshot of every instance, restore every instance
+ * exactly and keep the fastest (written to *best, may be NULL): regions with
+ * quanta 2 and 4 and tiles of 32 and 64 rows, and for the zero boundary
+ * register streaming with 2, 3 or 4 levels per launch (which also sets the
+ * strips' halo width, R T columns) and strips of 16, 32 or 64 rows. */
 int wave2d_batch_autotune(wave2d_batch_t b, const int64_t *steps, int64_t probe_steps,
                           wave2d_tune *best);
 
@@ -476,10 +484,13 @@ void wave2d_batch_destroy(wave2d_batch_t b);
 /* order while the device-memory budget and the slot limit allow, runs the   */
 /* first step (Eq. A1) of the newly admitted ones in one batched launch,     */
 /* advances every resident simulation by up to `quantum` two-steps (Eq. A2)  */
-/* per round in one batched run, and retires finished ones (FP64 norms to the */
-/* host, optional copy of the final level, memory released).  Requests that  */
-/* arrive while others run join at the next round.  A result does not depend  */
-/* on what else was resident (same per-node arithmetic as a single handle).  */
+/* per round in one batched run (the batch kept while its members stay), and */
+/* retires finished ones: their FP64 norms in one launch, copied to pinned   */
+/* host memory and collected once the copy has passed, their memory released */
+/* in stream order.  The host queues each round without waiting for the GPU  */
+/* and runs at most two rounds ahead of it.  Requests that arrive while       */
+/* others run join at the next round.  A result does not depend on what else  */
+/* was resident (same per-node arithmetic as a single handle).               */
 /* ------------------------------------------------------------------------ */
 typedef struct wave2d_server *wave2d_server_t;
 
@@ -499,7 +510,9 @@ typedef struct {
 
 typedef struct {
     uint64_t tag;
-    int32_t status;                /* WAVE2D_OK or the error of this request                */
+    int32_t status;                /* WAVE2D_OK, or the error of a step that failed for this
+                                      request: its l2 / linf are NaN and its levels are not
+                                      counted in node_updates                              */
     int32_t reserved;
     double l2, linf;               /* FP64 sqrt(sum u^2) and max |u| of the final level      */
     int64_t k;                     /* index of the final level                              */
@@ -509,15 +522,27 @@ typedef struct {
 typedef struct {
     int64_t submitted, completed, queued, node_updates, rounds, used_bytes;
     int32_t max_resident_seen, reserved;
+    double gpu_busy_s;             /* device time of the rounds (CUDA events around each
+                                      round's work on the server stream), seconds        */
 } wave2d_server_stats_t;
 
 /* Device bytes a handle of this size and type holds (the admission cost). */
 int64_t wave2d_required_bytes(int nx, int ny, int dtype);
 
 /* Start a server on the current device.  budget_bytes: device memory that
- * resident simulations may hold; max_resident: slot limit; quantum: two-steps
- * per round; opt (may be NULL): temporal_t (1..4) and tile_h (32 | 64) of the
- * batched runs; stream: cudaStream_t to use, NULL = a new one. */
+ * resident simulations may hold (their handles, wave2d_required_bytes each;
+ * the transient FP64 initial data of a round's pulse requests, 16 nx ny bytes
+ * each, and the batch tables are allocated on top of it for the duration of
+ * the round); max_resident: slot limit; quantum: two-steps per round; opt
+ * (may be NULL): kernel of the batched runs (WAVE2D_KERNEL_STREAM, the
+ * default, or WAVE2D_KERNEL_TEMPORAL), temporal_t (1..4 levels per launch)
+ * and tile_h (strip rows 8..1024 for streaming, else chosen per round as the
+ * tallest of 64, 32, 16 that gives a full wave of warps; 32 | 64 for
+ * regions); stream: cudaStream_t to use, NULL = a new one.
+ * Failures: a request whose step fails is completed with that status.  A
+ * failed allocation of a round's initial-data staging fails that round's
+ * pulse requests with WAVE2D_ERR_OOM and the server keeps serving; a CUDA
+ * error also latches a server-wide error that poll and drain return. */
 int wave2d_server_create(int64_t budget_bytes, int max_resident, int quantum, const wave2d_tune *opt,
                          void *stream, wave2d_server_t *out);
 

@@ -21,6 +21,7 @@
 #include <type_traits>
 #include <vector>
 
+#include "kernels_stream.cuh"
 #include "kernels_temporal.cuh"
 #include "wave2d_impl.cuh"
 
@@ -112,6 +113,43 @@ __global__ void __launch_bounds__(kBatchNW * 32, 1)
     const bool edge = PER && (tx * OW < gw || tx * OW + OW > g.nx - gw || ty * OH < gw || ty * OH + OH > g.ny - gw);
     region_store<PER, kBatchRVW, kBatchNW>((Ti & 1) ? P : Q, (Ti & 1) ? Q : P, HY, OH, Tq, OWV, gx0, gy0, g,
                                            I.planes[in_cur ^ 2], I.planes[in_prv ^ 2], gw, edge);
+}
+
+// Register-streaming batch (zero boundary): one warp per strip, over the
+// strips of all instances of one scheme in a launch.  Warp w finds its
+// instance by binary search over the strips' prefix sums and walks that
+// instance's strip exactly as the single-grid streaming kernel does
+// (stream_strip), T levels out of place into the other pair of planes; the
+// pairs alternate with the launch's parity q.
+struct StreamInst {
+    float* planes[4];
+    Geo g;
+    Coef3<float> a;
+    int cur0, prv0;  // planes of u^k and u^{k-1} at the instance's launch of parity 0
+    int strips_x;
+};
+
+template <int S, int T>
+__global__ void __launch_bounds__(kStreamWarps * 32)
+    k7_batch_stream(const StreamInst* __restrict__ insts, const int* __restrict__ strip_prefix, int n_active, int q,
+                    int L) {
+    constexpr int NB = StreamCfg<S, T>::NB;
+    extern __shared__ float4 stream_smem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int strip = blockIdx.x * kStreamWarps + warp;
+    if (strip >= __ldg(strip_prefix + n_active)) return;  // whole warps only
+    int lo = 0, hi = n_active;  // strip_prefix[lo] <= strip < strip_prefix[lo + 1]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(strip_prefix + mid) <= strip) lo = mid;
+        else hi = mid;
+    }
+    const StreamInst& I = insts[lo];
+    const int par = (q & 1) * 2;
+    const int ic = I.cur0 ^ par, ip = I.prv0 ^ par;
+    stream_strip<S, false, T, false>(I.planes[ic], I.planes[ip], I.planes[ic ^ 2], I.planes[ip ^ 2], I.g, I.a,
+                                     I.strips_x, strip - __ldg(strip_prefix + lo), L,
+                                     stream_smem + warp * NB * 2 * 32, lane);
 }
 
 // Batched first step (Eq. A1): one node per thread, blocks of 32 x 8 nodes
@@ -252,6 +290,19 @@ struct wave2d_batch {
     const void* plan_insts = nullptr;
     const int* plan_prefix = nullptr;
     int plan_smem = 0;
+    // register-streaming runs (WAVE2D_KERNEL_STREAM, zero boundary): one
+    // branch of launches per scheme on its own stream, forked from and joined
+    // to the batch stream
+    int kernel = WAVE2D_KERNEL_TEMPORAL;
+    int plan_kernel = 0;
+    struct SLaunch {
+        int scheme, T, grid, n_active, q, branch;
+        const void* insts;
+        const int* prefix;
+    };
+    std::vector<SLaunch> plan_slaunches;
+    cudaStream_t side[3] = {};
+    cudaEvent_t ev_fork = nullptr, ev_join[3] = {};
 };
 
 namespace {
@@ -281,6 +332,7 @@ void free_plan(wave2d_batch* b) {
         b->dev_bytes = 0;
     }
     b->plan_steps.clear();
+    b->plan_slaunches.clear();
 }
 
 int encode_region(CUtensorMap* tm, void* plane, const wave2d* h, int rh) {
@@ -406,6 +458,173 @@ int build_plan(wave2d_batch* b, const int64_t* steps) {
     return WAVE2D_OK;
 }
 
+// Plan of a register-streaming run: per scheme, the instances sorted by their
+// number of full launches (steps / T), one launch of T levels per quantum over
+// those still running, then one launch per remainder r = steps mod T (r levels)
+// over the instances that have it, each instance at the parity its full
+// launches left it in.
+int build_stream_plan(wave2d_batch* b, const int64_t* steps) {
+    free_plan(b);
+    const int n = (int)b->hs.size();
+    const int T = b->Tq, L = b->OH;
+    struct Table {
+        std::vector<StreamInst> insts;
+        std::vector<int> prefix;
+        int scheme, T, branch;
+        int64_t nq_max;  // full-launch tables: launches; remainder tables: 1
+        std::vector<int64_t> nq;  // full launches per instance (full-launch tables)
+    };
+    std::vector<Table> tables;
+    const int schemes[3] = {13, 9, 5};
+    for (int br = 0; br < 3; ++br) {
+        const int S = schemes[br];
+        std::vector<int> idx;
+        for (int i = 0; i < n; ++i)
+            if (b->hs[i]->scheme == S && steps[i] > 0) idx.push_back(i);
+        if (idx.empty()) continue;
+        std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) { return steps[x] / T > steps[y] / T; });
+        auto inst_of = [&](int i, int t, int flip) {
+            wave2d* h = b->hs[i];
+            StreamInst I{};
+            for (int p = 0; p < 4; ++p) I.planes[p] = reinterpret_cast<float*>(h->hi[p]);
+            I.g = h->geo();
+            I.a = Coef3<float>{(float)h->a[0], (float)h->a[1], (float)h->a[2]};
+            I.cur0 = h->cur ^ flip;
+            I.prv0 = h->prv ^ flip;
+            const int R = (S == 13) ? 2 : 1, HX = (R * t + 3) / 4 * 4, OW = 128 - 2 * HX;
+            I.strips_x = (h->nx + OW - 1) / OW;
+            return std::make_pair(I, I.strips_x * ((h->ny + L - 1) / L));
+        };
+        Table full;
+        full.scheme = S;
+        full.T = T;
+        full.branch = br;
+        full.prefix.push_back(0);
+        for (int i : idx) {
+            if (steps[i] / T == 0) break;
+            auto pr = inst_of(i, T, 0);
+            full.insts.push_back(pr.first);
+            full.prefix.push_back(full.prefix.back() + pr.second);
+            full.nq.push_back(steps[i] / T);
+        }
+        full.nq_max = full.nq.empty() ? 0 : full.nq[0];
+        if (!full.insts.empty()) tables.push_back(std::move(full));
+        for (int r = 1; r < T; ++r) {
+            Table rem;
+            rem.scheme = S;
+            rem.T = r;
+            rem.branch = br;
+            rem.nq_max = 1;
+            rem.prefix.push_back(0);
+            for (int i : idx) {
+                if (steps[i] % T != r) continue;
+                auto pr = inst_of(i, r, (int)((steps[i] / T) & 1) * 2);
+                rem.insts.push_back(pr.first);
+                rem.prefix.push_back(rem.prefix.back() + pr.second);
+            }
+            if (!rem.insts.empty()) tables.push_back(std::move(rem));
+        }
+    }
+    size_t bytes = 0;
+    std::vector<size_t> at(tables.size());
+    for (size_t t = 0; t < tables.size(); ++t) {
+        at[t] = bytes;
+        bytes += round_up(tables[t].insts.size() * sizeof(StreamInst), 256) +
+                 round_up(tables[t].prefix.size() * sizeof(int), 256);
+    }
+    b->dev_bytes = std::max<size_t>(bytes, 256);
+    b->dev = dev_alloc(b->alloc, b->dev_bytes, b->stream);
+    if (!b->dev) return set_error(WAVE2D_ERR_OOM, "batch table allocation failed");
+    b->plan_slaunches.clear();
+    for (size_t t = 0; t < tables.size(); ++t) {
+        Table& tb = tables[t];
+        char* base = (char*)b->dev + at[t];
+        StreamInst* di = (StreamInst*)base;
+        int* dp = (int*)(base + round_up(tb.insts.size() * sizeof(StreamInst), 256));
+        cudaError_t e = cudaMemcpyAsync(di, tb.insts.data(), tb.insts.size() * sizeof(StreamInst),
+                                        cudaMemcpyHostToDevice, b->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(dp, tb.prefix.data(), tb.prefix.size() * sizeof(int), cudaMemcpyHostToDevice, b->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "batch table upload");
+        int active = (int)tb.insts.size();
+        for (int64_t q = 0; q < tb.nq_max; ++q) {
+            if (!tb.nq.empty())
+                while (active > 0 && tb.nq[active - 1] <= q) --active;
+            if (active == 0) break;
+            const int grid = (tb.prefix[active] + kStreamWarps - 1) / kStreamWarps;
+            b->plan_slaunches.push_back({tb.scheme, tb.T, grid, active, (int)q, tb.branch, di, dp});
+        }
+    }
+    return WAVE2D_OK;  // pageable uploads return once the host tables may be released
+}
+
+template <int S>
+cudaError_t launch_k7(const wave2d_batch::SLaunch& l, int L, cudaStream_t st) {
+    switch (l.T) {
+        case 1: k7_batch_stream<S, 1><<<l.grid, kStreamWarps * 32, stream_smem_bytes<S, 1>(), st>>>(
+                    (const StreamInst*)l.insts, l.prefix, l.n_active, l.q, L); break;
+        case 2: k7_batch_stream<S, 2><<<l.grid, kStreamWarps * 32, stream_smem_bytes<S, 2>(), st>>>(
+                    (const StreamInst*)l.insts, l.prefix, l.n_active, l.q, L); break;
+        case 3: k7_batch_stream<S, 3><<<l.grid, kStreamWarps * 32, stream_smem_bytes<S, 3>(), st>>>(
+                    (const StreamInst*)l.insts, l.prefix, l.n_active, l.q, L); break;
+        default: k7_batch_stream<S, 4><<<l.grid, kStreamWarps * 32, stream_smem_bytes<S, 4>(), st>>>(
+                    (const StreamInst*)l.insts, l.prefix, l.n_active, l.q, L); break;
+    }
+    return cudaGetLastError();
+}
+
+// Issue the launches of a streaming plan: each scheme's launches in order on
+// its own stream, forked from the batch stream and joined back to it.
+int issue_stream_plan(wave2d_batch* b, int& launches) {
+    launches = 0;
+    bool used[3] = {false, false, false};
+    for (const auto& l : b->plan_slaunches) used[l.branch] = true;
+    cudaError_t e = cudaSuccess;
+    if (!b->ev_fork) e = cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming);
+    for (int br = 0; br < 3 && e == cudaSuccess; ++br) {  // created on first use, kept for the batch's life
+        if (!b->ev_join[br]) e = cudaEventCreateWithFlags(&b->ev_join[br], cudaEventDisableTiming);
+        if (e == cudaSuccess && !b->side[br]) e = cudaStreamCreateWithFlags(&b->side[br], cudaStreamNonBlocking);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "batch stream create");
+    e = cudaEventRecord(b->ev_fork, b->stream);
+    for (int br = 0; br < 3 && e == cudaSuccess; ++br)
+        if (used[br]) e = cudaStreamWaitEvent(b->side[br], b->ev_fork, 0);
+    for (const auto& l : b->plan_slaunches) {
+        if (e != cudaSuccess) break;
+        cudaStream_t st = b->side[l.branch];
+        e = l.scheme == 13 ? launch_k7<13>(l, b->OH, st) : l.scheme == 9 ? launch_k7<9>(l, b->OH, st)
+                                                                         : launch_k7<5>(l, b->OH, st);
+        ++launches;
+    }
+    for (int br = 0; br < 3 && e == cudaSuccess; ++br)
+        if (used[br]) {
+            e = cudaEventRecord(b->ev_join[br], b->side[br]);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->ev_join[br], 0);
+        }
+    if (e != cudaSuccess) return cuda_fail(e, "batched streaming launch");
+    return WAVE2D_OK;
+}
+
+int capture_stream_plan(wave2d_batch* b) {
+    if (b->direct) return WAVE2D_OK;
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(e, "begin capture");
+    int launches = 0;
+    const int rc = issue_stream_plan(b, launches);
+    e = cudaStreamEndCapture(b->stream, &graph);
+    if (rc != WAVE2D_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "end capture");
+    e = cudaGraphInstantiate(&b->graph, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(e, "graph instantiate");
+    b->graph_launches = launches;
+    return WAVE2D_OK;
+}
+
 // Launch the quanta of the current plan one by one (direct mode).
 int launch_direct(wave2d_batch* b) {
     const bool per = b->bc == WAVE2D_BC_PERIODIC;
@@ -422,8 +641,12 @@ int launch_direct(wave2d_batch* b) {
     return WAVE2D_OK;
 }
 
+bool stream_mode(const wave2d_batch* b) { return b->kernel == WAVE2D_KERNEL_STREAM && b->bc == WAVE2D_BC_ZERO; }
+
 bool same_plan(const wave2d_batch* b, const int64_t* steps) {
-    if ((!b->graph && !b->direct) || !b->dev || b->plan_Tq != b->Tq || b->plan_OH != b->OH || b->plan_steps.size() != b->hs.size()) return false;
+    if ((!b->graph && !b->direct) || !b->dev || b->plan_Tq != b->Tq || b->plan_OH != b->OH ||
+        b->plan_kernel != (stream_mode(b) ? 1 : 0) || b->plan_steps.size() != b->hs.size())
+        return false;
     for (size_t i = 0; i < b->hs.size(); ++i)
         if (b->plan_steps[i] != steps[i] || b->plan_start[i] != b->hs[i]->cur * 4 + b->hs[i]->prv) return false;
     return true;
@@ -433,13 +656,24 @@ int run_once(wave2d_batch* b, const int64_t* steps) {
     const int n = (int)b->hs.size();
     // A plan records each handle's starting planes (the pairs alternate per
     // quantum); it is replayed only when they and the step counts match.
+    const bool sm = stream_mode(b);
     if (!same_plan(b, steps)) {
-        int rc = build_plan(b, steps);
+        int rc = sm ? build_stream_plan(b, steps) : build_plan(b, steps);
+        if (rc == WAVE2D_OK && sm) rc = capture_stream_plan(b);
         if (rc != WAVE2D_OK) return rc;
+        b->plan_steps.assign(steps, steps + n);
+        b->plan_Tq = b->Tq;
+        b->plan_OH = b->OH;
+        b->plan_kernel = sm ? 1 : 0;
         b->plan_start.resize(n);
         for (int i = 0; i < n; ++i) b->plan_start[i] = b->hs[i]->cur * 4 + b->hs[i]->prv;
     }
-    if (b->direct) {
+    if (b->direct && sm) {
+        int launches = 0;
+        int rc = issue_stream_plan(b, launches);
+        if (rc != WAVE2D_OK) return rc;
+        g_launches.fetch_add(launches);
+    } else if (b->direct) {
         int rc = launch_direct(b);
         if (rc != WAVE2D_OK) return rc;
     } else {
@@ -466,6 +700,62 @@ int run_once(wave2d_batch* b, const int64_t* steps) {
 
 }  // namespace
 
+namespace w2d {
+
+// Replace the members of a batch (validated as at create: F32, one boundary
+// and device, no repeats) and drop its plan; its streams, events and tuning
+// stay.  For callers that advance a changing set of handles (the server).
+int batch_set_handles(wave2d_batch* b, wave2d_t* handles, int n, int rows) {
+    if (!b || !handles || n < 1) return set_error(WAVE2D_ERR_ARG, "batch needs at least one handle");
+    for (int i = 0; i < n; ++i)
+        if (!handles[i] || handles[i]->dtype != WAVE2D_F32 || handles[i]->bc != b->bc)
+            return set_error(WAVE2D_ERR_ARG, "batch member %d does not match the batch", i);
+    free_plan(b);
+    b->hs.assign(handles, handles + n);
+    if (rows > 0) b->OH = rows;
+    return WAVE2D_OK;
+}
+
+// FP64 sqrt(sum u^2) and max |u| of the current level of each handle (all on
+// stream st), written to host_out[2 i], host_out[2 i + 1] by an asynchronous
+// copy: host_out must be pinned and stay valid until st passes an event
+// recorded after this call.  Scratch is allocated and freed in stream order.
+int batch_norms_async(wave2d* const* hs, int n, cudaStream_t st, const Allocator& al, double* host_out) {
+    std::vector<BatchNorm> ns(n);
+    std::vector<int> prefix(n + 1, 0);
+    int chunks = 0;
+    for (int i = 0; i < n; ++i) {
+        const wave2d* h = hs[i];
+        ns[i].plane = reinterpret_cast<const float*>(h->hi[h->cur]);
+        ns[i].g = h->geo();
+        ns[i].blocks = (h->ny + 7) / 8;
+        ns[i].first = chunks;
+        chunks += ns[i].blocks;
+        prefix[i + 1] = chunks;
+    }
+    const size_t ns_bytes = round_up(n * sizeof(BatchNorm), 256), pre_bytes = round_up((n + 1) * sizeof(int), 256);
+    const size_t part_bytes = round_up(2 * (size_t)chunks * sizeof(double), 256);
+    const size_t total = ns_bytes + pre_bytes + part_bytes + 2 * n * sizeof(double);
+    char* dev = (char*)dev_alloc(al, total, st);
+    if (!dev) return set_error(WAVE2D_ERR_OOM, "batch norm allocation failed");
+    double* part = (double*)(dev + ns_bytes + pre_bytes);
+    double* res = (double*)(dev + ns_bytes + pre_bytes + part_bytes);
+    cudaError_t e = cudaMemcpyAsync(dev, ns.data(), n * sizeof(BatchNorm), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dev + ns_bytes, prefix.data(), (n + 1) * sizeof(int), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) {
+        k6_batch_norm_partial<<<chunks, 256, 0, st>>>((const BatchNorm*)dev, (const int*)(dev + ns_bytes), n, part);
+        k6_batch_norm_final<<<n, 32, 0, st>>>((const BatchNorm*)dev, part, res);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) g_launches.fetch_add(2);
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(host_out, res, 2 * n * sizeof(double), cudaMemcpyDeviceToHost, st);
+    dev_free(al, dev, total, st);
+    if (e != cudaSuccess) return cuda_fail(e, "batch norms");
+    return WAVE2D_OK;
+}
+
+}  // namespace w2d
+
 extern "C" {
 
 int wave2d_batch_create(wave2d_t* handles, int n, const wave2d_tune* opt, wave2d_batch_t* out) {
@@ -486,10 +776,17 @@ int wave2d_batch_create(wave2d_t* handles, int n, const wave2d_tune* opt, wave2d
         for (int j = 0; j < i; ++j)
             if (handles[j] == handles[i]) return set_error(WAVE2D_ERR_ARG, "handle %d appears twice", i);
     }
+    const bool stream_kernel = opt && opt->kernel == WAVE2D_KERNEL_STREAM;
+    if (opt && opt->kernel != 0 && opt->kernel != WAVE2D_KERNEL_TEMPORAL && !stream_kernel)
+        return set_error(WAVE2D_ERR_ARG, "batch kernel must be 0, WAVE2D_KERNEL_TEMPORAL or WAVE2D_KERNEL_STREAM");
+    if (stream_kernel && handles[0]->bc != WAVE2D_BC_ZERO)
+        return set_error(WAVE2D_ERR_ARG, "batched register streaming covers the zero boundary");
     if (opt && opt->temporal_t != 0 && (opt->temporal_t < 1 || opt->temporal_t > 4))
         return set_error(WAVE2D_ERR_ARG, "batch quantum must be 1..4 levels");
-    if (opt && opt->tile_h != 0 && opt->tile_h != 32 && opt->tile_h != 64)
+    if (opt && opt->tile_h != 0 && !stream_kernel && opt->tile_h != 32 && opt->tile_h != 64)
         return set_error(WAVE2D_ERR_ARG, "batch tile height must be 32 or 64");
+    if (opt && opt->tile_h != 0 && stream_kernel && (opt->tile_h < 8 || opt->tile_h > 1024))
+        return set_error(WAVE2D_ERR_ARG, "batch strip rows must be 8..1024");
     wave2d_batch* b = new (std::nothrow) wave2d_batch();
     if (!b) return set_error(WAVE2D_ERR_OOM, "host allocation failed");
     b->hs.assign(handles, handles + n);
@@ -497,6 +794,10 @@ int wave2d_batch_create(wave2d_t* handles, int n, const wave2d_tune* opt, wave2d
     b->alloc = handles[0]->alloc;
     b->bc = handles[0]->bc;
     b->num_sms = handles[0]->num_sms;
+    if (stream_kernel) {
+        b->kernel = WAVE2D_KERNEL_STREAM;
+        b->OH = 64;
+    }
     if (opt && opt->temporal_t) b->Tq = opt->temporal_t;
     if (opt && opt->tile_h) b->OH = opt->tile_h;
     b->direct = opt && opt->use_graph == 0;
@@ -511,8 +812,15 @@ int wave2d_batch_create(wave2d_t* handles, int n, const wave2d_tune* opt, wave2d
 
 void wave2d_batch_destroy(wave2d_batch_t b) {
     if (!b) return;
-    free_plan(b);
-    cudaStreamSynchronize(b->stream);
+    const bool graph = b->graph != nullptr;
+    free_plan(b);  // tables freed in stream order
+    // a captured run may still be executing; direct launches need no wait
+    if (graph || b->side[0] || b->side[1] || b->side[2]) cudaStreamSynchronize(b->stream);
+    for (int br = 0; br < 3; ++br) {
+        if (b->side[br]) cudaStreamDestroy(b->side[br]);
+        if (b->ev_join[br]) cudaEventDestroy(b->ev_join[br]);
+    }
+    if (b->ev_fork) cudaEventDestroy(b->ev_fork);
     if (b->ev) cudaEventDestroy(b->ev);
     delete b;
 }
@@ -582,7 +890,8 @@ static int batch_first_step_impl(wave2d_batch_t b, const double* const* u0, cons
             e = cudaGetLastError();
             if (e == cudaSuccess) g_launches.fetch_add(1);
         }
-        if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);  // host staging must outlive the copies
+        // pageable host arrays are staged by the copy calls themselves; only
+        // the device tables' uploads above need nothing more
         if (e != cudaSuccess) rc = cuda_fail(e, "batch first step");
     }
     dev_free(b->alloc, dev, total, b->stream);
@@ -686,12 +995,21 @@ static int batch_autotune_impl(wave2d_batch_t b, const int64_t* steps, int64_t p
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (rc == WAVE2D_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
         rc = set_error(WAVE2D_ERR_CUDA, "event create failed");
-    const int cands[4][2] = {{2, 32}, {2, 64}, {4, 32}, {4, 64}};
+    // candidates: (kernel, levels per launch, rows per tile or strip); the
+    // register-streaming batch for the zero boundary
+    struct Cand { int kernel, T, rows; };
+    std::vector<Cand> cands = {{WAVE2D_KERNEL_TEMPORAL, 2, 32}, {WAVE2D_KERNEL_TEMPORAL, 2, 64},
+                               {WAVE2D_KERNEL_TEMPORAL, 4, 32}, {WAVE2D_KERNEL_TEMPORAL, 4, 64}};
+    if (b->bc == WAVE2D_BC_ZERO)
+        for (int T : {2, 3, 4})
+            for (int rows : {16, 32, 64}) cands.push_back({WAVE2D_KERNEL_STREAM, T, rows});
+    const int kernel0 = b->kernel, T0 = b->Tq, OH0 = b->OH;
     float best_ms = -1;
-    int best_c = 2;
-    for (int c = 0; c < 4 && rc == WAVE2D_OK; ++c) {
-        b->Tq = cands[c][0];
-        b->OH = cands[c][1];
+    int best_c = -1;
+    for (int c = 0; c < (int)cands.size() && rc == WAVE2D_OK; ++c) {
+        b->kernel = cands[c].kernel;
+        b->Tq = cands[c].T;
+        b->OH = cands[c].rows;
         rc = copy_all(false);
         if (rc == WAVE2D_OK) rc = run_once(b, probe.data());  // builds the plan and warms up
         if (rc == WAVE2D_OK) rc = copy_all(false);
@@ -718,11 +1036,18 @@ static int batch_autotune_impl(wave2d_batch_t b, const int64_t* steps, int64_t p
     dev_free(b->alloc, snap, snap_bytes, b->stream);
     free_plan(b);
     if (rc == WAVE2D_OK) rc = rc2;
-    b->Tq = cands[best_c][0];
-    b->OH = cands[best_c][1];
+    if (best_c >= 0) {
+        b->kernel = cands[best_c].kernel;
+        b->Tq = cands[best_c].T;
+        b->OH = cands[best_c].rows;
+    } else {
+        b->kernel = kernel0;
+        b->Tq = T0;
+        b->OH = OH0;
+    }
     if (best) {
         std::memset(best, 0, sizeof *best);
-        best->kernel = WAVE2D_KERNEL_TEMPORAL;
+        best->kernel = b->kernel;
         best->temporal_t = b->Tq;
         best->tile_h = b->OH;
     }

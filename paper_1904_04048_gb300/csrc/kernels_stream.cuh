@@ -276,27 +276,25 @@ __device__ __forceinline__ void stream_group(const StreamWarp& w, const Geo& g, 
     });
 }
 
-// in_cur / in_prev: planes of u^k and u^{k-1}; out_cur / out_prev: planes
-// that receive u^{k+T} and u^{k+T-1}.  Strip s covers output columns
-// [x0, x0 + OW) with x0 = (s % strips_x) OW and rows [y0, y0 + L) with
-// y0 = (s / strips_x) L.
+// One warp's walk down strip `strip` of a grid: in_cur / in_prev are the
+// planes of u^k and u^{k-1}; out_cur / out_prev receive u^{k+T} and
+// u^{k+T-1}.  Strip s covers output columns [x0, x0 + OW) with
+// x0 = (s % strips_x) OW and rows [y0, y0 + L) with y0 = (s / strips_x) L.
+// ring: this warp's NB input row slots (both planes) in shared memory.
 template <int S, bool PER, int T, bool WRAP>
-__global__ void __launch_bounds__(kStreamWarps * 32)
-    k5_stream(const float* __restrict__ in_cur, const float* __restrict__ in_prev, float* __restrict__ out_cur,
-              float* __restrict__ out_prev, Geo g, Coef3<float> a, int strips_x, int n_strips, int L) {
+__device__ __forceinline__ void stream_strip(const float* __restrict__ in_cur, const float* __restrict__ in_prev,
+                                             float* __restrict__ out_cur, float* __restrict__ out_prev,
+                                             const Geo& g, const Coef3<float>& a, int strips_x, int strip, int L,
+                                             float4* ring, int lane) {
     using C = StreamCfg<S, T>;
     constexpr int R = C::R, D = C::D, WIN = C::WIN, HX = C::HX, OW = C::OW, NB = C::NB, PF = C::PF;
-    extern __shared__ float4 stream_smem[];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int strip = blockIdx.x * kStreamWarps + warp;
-    if (strip >= n_strips) return;  // whole warps only; no copies issued yet
     const int x0 = (strip % strips_x) * OW, y0 = (strip / strips_x) * L;
     StreamWarp w;
     w.in_cur = in_cur;
     w.in_prev = in_prev;
     w.out_cur = out_cur;
     w.out_prev = out_prev;
-    w.ring = stream_smem + warp * NB * 2 * 32;
+    w.ring = ring;
     w.lane = lane;
     w.xl = x0 - HX + 4 * lane;                  // grid column of the lane's first node (>= -G)
     w.xload = min(w.xl, g.pitch - g.G - 4);     // inside the row's storage; clamped lanes are
@@ -330,6 +328,21 @@ __global__ void __launch_bounds__(kStreamWarps * 32)
     cp_async_wait_all();  // no copy may land in shared memory after the warp exits
 }
 
+// One grid: warp (blockIdx.x * kStreamWarps + warp) walks strip of that
+// index (strips_x strips across, n_strips in all).
+template <int S, bool PER, int T, bool WRAP>
+__global__ void __launch_bounds__(kStreamWarps * 32)
+    k5_stream(const float* __restrict__ in_cur, const float* __restrict__ in_prev, float* __restrict__ out_cur,
+              float* __restrict__ out_prev, Geo g, Coef3<float> a, int strips_x, int n_strips, int L) {
+    constexpr int NB = StreamCfg<S, T>::NB;
+    extern __shared__ float4 stream_smem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int strip = blockIdx.x * kStreamWarps + warp;
+    if (strip >= n_strips) return;  // whole warps only; no copies issued yet
+    stream_strip<S, PER, T, WRAP>(in_cur, in_prev, out_cur, out_prev, g, a, strips_x, strip, L,
+                                  stream_smem + warp * NB * 2 * 32, lane);
+}
+
 // Periodic images of the two levels a streaming launch wrote, in the first gw
 // rings, each ring cell copying the grid node it images.  Blocks with
 // blockIdx.y < 2 gw copy one row of the top (y < gw) or bottom band over the
@@ -342,7 +355,7 @@ __device__ __forceinline__ int wrap_index(int i, int n) {
     return ((i % n) + n) % n;  // grids narrower than the ring
 }
 
-__global__ void __launch_bounds__(256) k5_ring_images(float* __restrict__ a, float* __restrict__ b, Geo g, int gw) {
+static __global__ void __launch_bounds__(256) k5_ring_images(float* __restrict__ a, float* __restrict__ b, Geo g, int gw) {
     float* p = blockIdx.z ? b : a;
     const int t = threadIdx.x;
     if ((int)blockIdx.y < 2 * gw) {

@@ -57,6 +57,8 @@ struct Active {
     int64_t remaining = 0;
     int64_t bytes = 0;
     double t_admit = 0;
+    int failed = WAVE2D_OK;  // status of a step that failed for this request (it is retired with it)
+    uint64_t id = 0;         // admission number: identifies the simulation (a handle's address may recur)
 };
 
 }  // namespace
@@ -68,7 +70,8 @@ struct wave2d_server {
     int64_t budget = 0;
     int max_resident = 0;
     int quantum = 64;
-    int Tq = 4, OH = 32;
+    int kernel = WAVE2D_KERNEL_STREAM;  // batched runs: register streaming (the zero boundary of every request)
+    int Tq = 4, OH = 64;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     int device = 0;
@@ -86,6 +89,28 @@ struct wave2d_server {
     int fatal = 0;
     std::string fatal_msg;
     std::thread worker;
+    // pipeline (scheduler thread only): the batch that advances the resident
+    // set, requests whose norms are on their way to the host, and the rounds
+    // still executing (bounded, and timed for the busy fraction)
+    wave2d_batch_t batch = nullptr;
+    std::vector<uint64_t> batch_members;  // admission numbers of the batch's members, in order
+    uint64_t next_id = 1;
+    int batch_rows = 0;     // strip rows of the batch's current plan
+    bool auto_rows = true;  // strip rows chosen per round (false: fixed by opt->tile_h)
+    int num_sms = 0;
+    struct Retiring {
+        std::vector<Active> items;
+        double* norms = nullptr;  // pinned, two per item
+        size_t cap = 0;
+        cudaEvent_t ev = nullptr;
+    };
+    std::deque<Retiring> retiring;
+    std::vector<std::pair<double*, size_t>> pinned_pool;
+    struct Mark {
+        cudaEvent_t start = nullptr, end = nullptr;
+    };
+    std::deque<Mark> marks;
+    double busy_s = 0;
 };
 
 namespace {
@@ -126,8 +151,79 @@ void complete(wave2d_server* s, Active& a, int status, double l2, double linf, i
     s->done_cv.notify_all();
 }
 
-// One scheduling round; returns false when there is nothing to do.
+double* pinned_get(wave2d_server* s, size_t n, size_t& cap) {
+    for (size_t i = 0; i < s->pinned_pool.size(); ++i)
+        if (s->pinned_pool[i].second >= n) {
+            auto pr = s->pinned_pool[i];
+            s->pinned_pool.erase(s->pinned_pool.begin() + i);
+            cap = pr.second;
+            return pr.first;
+        }
+    double* p = nullptr;
+    cap = std::max<size_t>(n, 64);
+    if (cudaMallocHost(&p, cap * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+
+// Collect finished work: rounds whose end mark has passed (their GPU time),
+// and retirements whose norms have arrived (their completions).  block:
+// wait for the oldest round or retirement first.
+void reap(wave2d_server* s, bool block) {
+    if (block) {
+        if (!s->retiring.empty()) cudaEventSynchronize(s->retiring.front().ev);
+        else if (!s->marks.empty()) cudaEventSynchronize(s->marks.front().end);
+    }
+    while (!s->marks.empty()) {
+        auto& m = s->marks.front();
+        const cudaError_t q = cudaEventQuery(m.end);
+        if (q == cudaErrorNotReady) break;
+        float ms = 0;
+        if (q == cudaSuccess && cudaEventElapsedTime(&ms, m.start, m.end) == cudaSuccess) {
+            std::lock_guard<std::mutex> lk(s->mu);
+            s->busy_s += ms * 1e-3;
+        }
+        cudaGetLastError();
+        cudaEventDestroy(m.start);
+        cudaEventDestroy(m.end);
+        s->marks.pop_front();
+    }
+    while (!s->retiring.empty()) {
+        auto& r = s->retiring.front();
+        const cudaError_t q = cudaEventQuery(r.ev);
+        if (q == cudaErrorNotReady) break;
+        int rc = WAVE2D_OK;
+        if (q != cudaSuccess) {
+            rc = cuda_fail(q, "batched norms");
+            fail_round(s, rc);
+        }
+        for (size_t i = 0; i < r.items.size(); ++i) {
+            Active& a = r.items[i];
+            double l2 = NAN, linf = NAN;
+            int st = rc;
+            if (rc == WAVE2D_OK) {
+                l2 = r.norms[2 * i];
+                linf = r.norms[2 * i + 1];
+                if (!std::isfinite(l2) || !std::isfinite(linf)) st = WAVE2D_ERR_NONFINITE;
+            }
+            complete(s, a, st, l2, linf, a.p.r.steps + 1);
+        }
+        if (r.norms) s->pinned_pool.push_back({r.norms, r.cap});
+        cudaEventDestroy(r.ev);
+        s->retiring.pop_front();
+    }
+}
+
+// One scheduling round; returns false when there is nothing to do.  The host
+// queues a round's work (first steps of the admitted requests, one quantum of
+// every resident simulation, the norms of those that finish) without waiting
+// for the GPU, and runs at most two rounds ahead of it.
 bool round_once(wave2d_server* s) {
+    reap(s, false);
+    while (s->marks.size() >= 2) reap(s, true);
+
     // 1. admission (FIFO, budget and slots)
     std::vector<Active> admitted;
     {
@@ -141,12 +237,19 @@ bool round_once(wave2d_server* s) {
             a.bytes = need;
             a.t_admit = now_s();
             a.remaining = a.p.r.steps;
+            a.id = s->next_id++;
             s->used += need;
             admitted.push_back(std::move(a));
             s->queue.pop_front();
         }
     }
-    if (admitted.empty() && s->resident.empty()) return false;
+    if (admitted.empty() && s->resident.empty()) {
+        if (s->retiring.empty() && s->marks.empty()) return false;
+        reap(s, true);
+        return true;
+    }
+    cudaEvent_t ev_start = nullptr, ev_end = nullptr;
+    if (cudaEventCreate(&ev_start) == cudaSuccess) cudaEventRecord(ev_start, s->stream);
 
     // 2. create handles and run the first step of the admitted requests
     if (!admitted.empty()) {
@@ -187,7 +290,11 @@ bool round_once(wave2d_server* s) {
             int rc = wave2d_batch_create(hs_host.data(), (int)hs_host.size(), &opt, &b);
             if (rc == WAVE2D_OK) rc = wave2d_batch_first_step(b, u_host.data(), v_host.data(), 0);
             wave2d_batch_destroy(b);
-            if (rc != WAVE2D_OK) fail_round(s, rc);
+            if (rc != WAVE2D_OK) {
+                for (Active& a : admitted)
+                    if (!a.p.u0.empty()) a.failed = rc;
+                fail_round(s, rc);
+            }
         }
         if (!hs_pulse.empty()) {
             size_t total = 0;
@@ -195,7 +302,9 @@ bool round_once(wave2d_server* s) {
             Allocator al = current_allocator();
             double* stage = (double*)dev_alloc(al, total * sizeof(double), s->stream);
             if (!stage) {
-                fail_round(s, set_error(WAVE2D_ERR_OOM, "initial-data staging allocation failed"));
+                // the requests of this round fail; the server keeps serving
+                const int rc = set_error(WAVE2D_ERR_OOM, "initial-data staging allocation failed");
+                for (Active* a : pulses) a->failed = rc;
             } else {
                 std::vector<const double*> pu, pv;
                 double* p = stage;
@@ -213,63 +322,129 @@ bool round_once(wave2d_server* s) {
                 int rc = wave2d_batch_create(hs_pulse.data(), (int)hs_pulse.size(), &opt, &b);
                 if (rc == WAVE2D_OK) rc = wave2d_batch_first_step(b, pu.data(), pv.data(), 1);
                 wave2d_batch_destroy(b);
-                dev_free(al, stage, total * sizeof(double), s->stream);
-                if (rc != WAVE2D_OK) fail_round(s, rc);
+                dev_free(al, stage, total * sizeof(double), s->stream);  // in stream order, after the first step
+                if (rc != WAVE2D_OK) {
+                    for (Active* a : pulses) a->failed = rc;
+                    fail_round(s, rc);
+                }
             }
         }
         int64_t first_nodes = 0;
         for (Active& a : admitted) {
-            first_nodes += (int64_t)a.p.r.nx * a.p.r.ny;
+            if (a.failed == WAVE2D_OK) first_nodes += (int64_t)a.p.r.nx * a.p.r.ny;
             s->resident.push_back(std::move(a));
         }
         std::lock_guard<std::mutex> lk(s->mu);
         s->node_updates += first_nodes;  // the first level of each request
         s->max_resident_seen = std::max<int>(s->max_resident_seen, (int)s->resident.size());
     }
-    if (s->resident.empty()) return true;
 
-    // 3. advance every resident simulation by up to one quantum
+    // 3. advance every resident simulation (not failed) by up to one quantum,
+    //    with the batch kept from round to round while its members stay
     std::vector<wave2d_t> hs;
-    std::vector<int64_t> steps;
-    for (Active& a : s->resident) {
-        hs.push_back(a.h);
-        steps.push_back(std::min<int64_t>(a.remaining, s->quantum));
-    }
+    std::vector<uint64_t> ids;
+    std::vector<int64_t> steps(s->resident.size(), 0), run_steps;
     int64_t nodes = 0;
-    for (size_t i = 0; i < hs.size(); ++i) nodes += (int64_t)s->resident[i].p.r.nx * s->resident[i].p.r.ny * steps[i];
-    {
-        wave2d_tune opt{};
-        opt.use_graph = 0;
-        opt.temporal_t = s->Tq;
-        opt.tile_h = s->OH;
-        wave2d_batch_t b = nullptr;
-        int rc = wave2d_batch_create(hs.data(), (int)hs.size(), &opt, &b);
-        if (rc == WAVE2D_OK) rc = wave2d_batch_run(b, steps.data());
-        wave2d_batch_destroy(b);  // synchronises the stream
-        if (rc != WAVE2D_OK) fail_round(s, rc);
-    }
-
-    // 4. retire finished simulations
-    std::vector<Active> still;
     for (size_t i = 0; i < s->resident.size(); ++i) {
         Active& a = s->resident[i];
-        a.remaining -= steps[i];
-        if (a.remaining > 0) {
-            still.push_back(std::move(a));
+        if (a.failed != WAVE2D_OK) continue;
+        steps[i] = std::min<int64_t>(a.remaining, s->quantum);
+        hs.push_back(a.h);
+        ids.push_back(a.id);
+        run_steps.push_back(steps[i]);
+        nodes += (int64_t)a.p.r.nx * a.p.r.ny * steps[i];
+    }
+    if (!hs.empty()) {
+        int rc = WAVE2D_OK;
+        // Register streaming: the tallest strips (64, 32 or 16 rows) that still
+        // give a full wave of warps over the resident set; few resident
+        // simulations make short launches, which keep the round (and so the
+        // latency of every request in it) short.
+        int rows = s->OH;
+        if (s->kernel == WAVE2D_KERNEL_STREAM && s->auto_rows) {
+            const int wave = 16 * std::max(1, s->num_sms);
+            rows = 16;
+            for (int L : {64, 32}) {
+                int64_t strips = 0;
+                for (wave2d_t h : hs) strips += (int64_t)((h->nx + 111) / 112) * ((h->ny + L - 1) / L);
+                if (strips >= wave) {
+                    rows = L;
+                    break;
+                }
+            }
+        }
+        if (!s->batch) {
+            wave2d_tune opt{};
+            opt.use_graph = 0;
+            opt.kernel = s->kernel;
+            opt.temporal_t = s->Tq;
+            opt.tile_h = rows;
+            rc = wave2d_batch_create(hs.data(), (int)hs.size(), &opt, &s->batch);
+            if (rc == WAVE2D_OK) s->batch_members = ids;
+            s->batch_rows = rows;
+        } else if (ids != s->batch_members || rows != s->batch_rows) {
+            rc = batch_set_handles(s->batch, hs.data(), (int)hs.size(), rows);
+            if (rc == WAVE2D_OK) s->batch_members = ids;
+            s->batch_rows = rows;
+        }
+        if (rc == WAVE2D_OK) rc = wave2d_batch_run(s->batch, run_steps.data());
+        if (rc != WAVE2D_OK) {
+            // every simulation of the failed run is retired with its status;
+            // none of its levels count as done
+            for (Active& a : s->resident)
+                if (a.failed == WAVE2D_OK) a.failed = rc;
+            nodes = 0;
+            fail_round(s, rc);
+        }
+    }
+
+    // 4. retire finished and failed simulations: the norms of those that
+    //    finished in one launch, copied to pinned memory and collected when
+    //    the copy's event has passed; handles released in stream order
+    std::vector<Active> still, finishing;
+    for (size_t i = 0; i < s->resident.size(); ++i) {
+        Active& a = s->resident[i];
+        if (a.failed != WAVE2D_OK) {
+            release_handle_nosync(a.h);
+            a.h = nullptr;
+            complete(s, a, a.failed, NAN, NAN, 0);
             continue;
         }
-        double l2 = NAN, linf = NAN;
-        int rc = wave2d_error_vs_exact(a.h, nullptr, &l2, &linf, nullptr);
-        if (a.p.r.out_field && (rc == WAVE2D_OK || rc == WAVE2D_ERR_NONFINITE))
-            wave2d_get_state(a.h, nullptr, a.p.r.out_field, nullptr);
-        int64_t k = 0;
-        wave2d_info_t info;
-        if (wave2d_get_info(a.h, &info) == WAVE2D_OK) k = info.k;
-        wave2d_destroy(a.h);
-        a.h = nullptr;
-        complete(s, a, rc, l2, linf, k);
+        a.remaining -= steps[i];
+        if (a.remaining > 0) still.push_back(std::move(a));
+        else finishing.push_back(std::move(a));
     }
     s->resident.swap(still);
+    if (!finishing.empty()) {
+        wave2d_server::Retiring r;
+        std::vector<wave2d*> fh;
+        for (Active& a : finishing) fh.push_back(a.h);
+        r.norms = pinned_get(s, 2 * finishing.size(), r.cap);
+        int rc = r.norms ? batch_norms_async(fh.data(), (int)fh.size(), s->stream, current_allocator(), r.norms)
+                         : set_error(WAVE2D_ERR_OOM, "pinned norm buffer allocation failed");
+        if (rc == WAVE2D_OK && cudaEventCreateWithFlags(&r.ev, cudaEventDisableTiming) != cudaSuccess)
+            rc = set_error(WAVE2D_ERR_CUDA, "event create failed");
+        for (Active& a : finishing) {
+            if (rc == WAVE2D_OK && a.p.r.out_field)
+                wave2d_get_state(a.h, nullptr, a.p.r.out_field, nullptr);  // synchronises: only when asked
+            release_handle_nosync(a.h);
+            a.h = nullptr;
+        }
+        if (rc == WAVE2D_OK) {
+            cudaEventRecord(r.ev, s->stream);
+            r.items = std::move(finishing);
+            s->retiring.push_back(std::move(r));
+        } else {
+            if (r.norms) s->pinned_pool.push_back({r.norms, r.cap});
+            for (Active& a : finishing) complete(s, a, rc, NAN, NAN, 0);
+        }
+    }
+    if (ev_start && cudaEventCreate(&ev_end) == cudaSuccess) {
+        cudaEventRecord(ev_end, s->stream);
+        s->marks.push_back({ev_start, ev_end});
+    } else if (ev_start) {
+        cudaEventDestroy(ev_start);
+    }
     {
         std::lock_guard<std::mutex> lk(s->mu);
         s->node_updates += nodes;
@@ -281,16 +456,27 @@ bool round_once(wave2d_server* s) {
 void worker_main(wave2d_server* s) {
     cudaSetDevice(s->device);
     for (;;) {
+        bool idle = false;
         {
             std::unique_lock<std::mutex> lk(s->mu);
-            if (s->stop && s->queue.empty() && s->resident.empty()) break;
-            if (s->queue.empty() && s->resident.empty()) {
+            const bool empty = s->queue.empty() && s->resident.empty();
+            if (s->stop && empty && s->retiring.empty() && s->marks.empty()) break;
+            if (empty && s->retiring.empty() && s->marks.empty()) {
                 s->cv.wait_for(lk, std::chrono::milliseconds(2));
                 continue;
             }
+            idle = empty;
         }
-        round_once(s);
+        if (idle) reap(s, true);  // only results in flight: collect them
+        else round_once(s);
     }
+    if (s->batch) {
+        wave2d_batch_destroy(s->batch);
+        s->batch = nullptr;
+    }
+    cudaStreamSynchronize(s->stream);
+    for (auto& pr : s->pinned_pool) cudaFreeHost(pr.first);
+    s->pinned_pool.clear();
 }
 
 }  // namespace
@@ -313,9 +499,18 @@ int wave2d_server_create(int64_t budget_bytes, int max_resident, int quantum, co
     s->budget = budget_bytes;
     s->max_resident = max_resident;
     s->quantum = quantum;
+    if (opt && opt->kernel == WAVE2D_KERNEL_TEMPORAL) {
+        s->kernel = WAVE2D_KERNEL_TEMPORAL;
+        s->OH = 32;
+    }
     if (opt && opt->temporal_t >= 1 && opt->temporal_t <= 4) s->Tq = opt->temporal_t;
-    if (opt && (opt->tile_h == 32 || opt->tile_h == 64)) s->OH = opt->tile_h;
+    if (opt && s->kernel == WAVE2D_KERNEL_TEMPORAL && (opt->tile_h == 32 || opt->tile_h == 64)) s->OH = opt->tile_h;
+    if (opt && s->kernel == WAVE2D_KERNEL_STREAM && opt->tile_h >= 8 && opt->tile_h <= 1024) {
+        s->OH = opt->tile_h;
+        s->auto_rows = false;
+    }
     cudaError_t e = cudaGetDevice(&s->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, s->device);
     s->stream = (cudaStream_t)stream;
     if (e == cudaSuccess && !s->stream) {
         e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
@@ -395,6 +590,7 @@ int wave2d_server_stats(wave2d_server_t s, wave2d_server_stats_t* st) {
     st->rounds = s->rounds;
     st->used_bytes = s->used;
     st->max_resident_seen = s->max_resident_seen;
+    st->gpu_busy_s = s->busy_s;
     return WAVE2D_OK;
 }
 

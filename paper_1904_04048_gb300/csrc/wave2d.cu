@@ -1483,3 +1483,18 @@ int wave2d_sync(wave2d_t h) {
 }
 
 }  // extern "C"
+
+namespace w2d {
+// Release a handle that shares its stream with its owner without waiting:
+// the memory is freed in stream order, after the work already queued.
+void release_handle_nosync(wave2d* h) {
+    if (!h) return;
+    if (h->own_stream) {
+        release_handle(h);
+        return;
+    }
+    drop_graphs(h);
+    if (h->base) dev_free(h->alloc, h->base, h->base_bytes, h->stream);
+    delete h;
+}
+}  // namespace w2d

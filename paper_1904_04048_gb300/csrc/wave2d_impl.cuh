@@ -133,6 +133,12 @@ int stream_fresh_rings(wave2d* h);
 // Guard-band canaries (canary.cu): fill the untouched cells of every plane
 // when the handle has WAVE2D_CANARY.
 int canary_fill(wave2d* h);
+// Server support (batch.cu, wave2d.cu): replace a batch's members keeping its
+// streams and tuning; batched norms copied to pinned host memory without a
+// wait; release a handle in stream order without a wait.
+int batch_set_handles(wave2d_batch* b, wave2d_t* handles, int n, int rows = 0);
+int batch_norms_async(wave2d* const* hs, int n, cudaStream_t st, const Allocator& al, double* host_out);
+void release_handle_nosync(wave2d* h);
 // Derivation and stability limit (scheme.cu).
 int derive_scheme(int m, wave2d_scheme* out);
 int check_scheme(const wave2d_scheme* s);

@@ -97,7 +97,7 @@ class wave2d_completion(ctypes.Structure):
 class wave2d_server_stats_t(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("queued", ctypes.c_int64),
                 ("node_updates", ctypes.c_int64), ("rounds", ctypes.c_int64), ("used_bytes", ctypes.c_int64),
-                ("max_resident_seen", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("max_resident_seen", ctypes.c_int32), ("reserved", ctypes.c_int32), ("gpu_busy_s", ctypes.c_double)]
 
 
 class wave2d_alu_peaks_t(ctypes.Structure):
@@ -471,10 +471,13 @@ class Wave2D:
 class Batch:
     """A batch of handles stepped together (``wave2d_batch_t``)."""
 
-    def __init__(self, sims, temporal_t=0, tile_h=0):
+    def __init__(self, sims, temporal_t=0, tile_h=0, kernel=KERNEL_TEMPORAL):
+        """kernel: KERNEL_TEMPORAL (shared-memory regions, any boundary) or
+        KERNEL_STREAM (register streaming, zero boundary); tile_h: rows per
+        region (32, 64) or per strip (8..1024); temporal_t: levels per launch."""
         self.sims = list(sims)
         arr = (ctypes.c_void_p * len(self.sims))(*[s.handle.value for s in self.sims])
-        opt = wave2d_tune(KERNEL_TEMPORAL, int(tile_h), int(temporal_t), -1, 0)
+        opt = wave2d_tune(int(kernel), int(tile_h), int(temporal_t), -1, 0)
         out = ctypes.c_void_p()
         check(lib().wave2d_batch_create(arr, len(self.sims), ctypes.byref(opt), ctypes.byref(out)))
         self._b = out
@@ -535,8 +538,9 @@ class Batch:
 class Server:
     """Continuous-batching server (``wave2d_server_t``)."""
 
-    def __init__(self, budget_bytes=16 << 30, max_resident=512, quantum=64, temporal_t=0, tile_h=0, stream=None):
-        opt = wave2d_tune(KERNEL_TEMPORAL, int(tile_h), int(temporal_t), 0, 0)
+    def __init__(self, budget_bytes=16 << 30, max_resident=512, quantum=64, temporal_t=0, tile_h=0, stream=None,
+                 kernel=KERNEL_STREAM):
+        opt = wave2d_tune(int(kernel), int(tile_h), int(temporal_t), 0, 0)
         out = ctypes.c_void_p()
         check(lib().wave2d_server_create(int(budget_bytes), int(max_resident), int(quantum), ctypes.byref(opt),
                                          ctypes.c_void_p(int(stream) if stream else 0), ctypes.byref(out)))

@@ -61,11 +61,18 @@ def make_handles(w, insts, bc):
 
 
 @pytest.mark.parametrize("bc", [BC_ZERO, BC_PERIODIC], ids=["zero", "periodic"])
-@pytest.mark.parametrize("Tq,oh", [(4, 32), (2, 64), (3, 32), (1, 32)])
-def test_batch_equals_alone_bitwise(w, bc, Tq, oh):
-    insts = mixed_instances(bc, seed=Tq)
+@pytest.mark.parametrize("Tq,oh,kernel", [(4, 32, "regions"), (2, 64, "regions"), (3, 32, "regions"),
+                                          (1, 32, "regions"), (4, 64, "stream"), (3, 16, "stream"),
+                                          (2, 37, "stream"), (1, 8, "stream")])
+def test_batch_equals_alone_bitwise(w, bc, Tq, oh, kernel):
+    """Shared-memory regions (any boundary) and register streaming (zero
+    boundary) end every instance where its own handle ends."""
+    if kernel == "stream" and bc != BC_ZERO:
+        pytest.skip("batched register streaming covers the zero boundary")
+    kern = w.KERNEL_STREAM if kernel == "stream" else w.KERNEL_TEMPORAL
+    insts = mixed_instances(bc, seed=Tq + oh)
     sims = make_handles(w, insts, bc)
-    with w.Batch(sims, temporal_t=Tq, tile_h=oh) as b:
+    with w.Batch(sims, temporal_t=Tq, tile_h=oh, kernel=kern) as b:
         b.first_step([d["u0"] for d in insts], [d["v0"] for d in insts])
         b.run([d["steps"] for d in insts])
         for d, s in zip(insts, sims):
@@ -173,4 +180,65 @@ def test_batch_argument_errors(w):
             bb.run([3])
         assert e.value.code == w.ERR_STATE
     for s in (a, b, c):
+        s.close()
+
+
+def test_stream_batch_reuse_direct_and_periodic_refusal(w):
+    """Register-streaming batches: a repeated run replays its graph, direct
+    launches (no graph) give the same bits, and a periodic batch is refused."""
+    import ctypes
+    insts = mixed_instances(BC_ZERO, seed=21, count=10)
+    sims = make_handles(w, insts, BC_ZERO)
+    steps = [d["steps"] for d in insts]
+    with w.Batch(sims, kernel=w.KERNEL_STREAM, temporal_t=4, tile_h=32) as b:
+        b.first_step([d["u0"] for d in insts], [d["v0"] for d in insts])
+        b.run(steps)
+        b.run(steps)
+    # direct launches: wave2d_batch_create with use_graph = 0
+    arr = (ctypes.c_void_p * len(sims))(*[s.handle.value for s in sims])
+    opt = w.wave2d_tune(w.KERNEL_STREAM, 32, 4, 0, 0)
+    bp = ctypes.c_void_p()
+    w.check(w.lib().wave2d_batch_create(arr, len(sims), ctypes.byref(opt), ctypes.byref(bp)))
+    try:
+        st = (ctypes.c_int64 * len(sims))(*[3] * len(sims))
+        w.check(w.lib().wave2d_batch_run(bp, st))
+    finally:
+        w.lib().wave2d_batch_destroy(bp)
+    for d, s in zip(insts, sims):
+        _, uc, k = s.get_state()
+        _, rc, rk = alone(w, d, BC_ZERO, 2 * d["steps"] + 3)
+        assert k == rk and np.array_equal(uc, rc)
+    for s in sims:
+        s.close()
+    psims = make_handles(w, mixed_instances(BC_PERIODIC, seed=2, count=3), BC_PERIODIC)
+    with pytest.raises(w.Wave2DError) as e:
+        w.Batch(psims, kernel=w.KERNEL_STREAM)
+    assert e.value.code == w.ERR_ARG
+    for s in psims:
+        s.close()
+
+
+def test_zero_boundary_autotune_covers_streaming_and_restores(w):
+    """On the zero boundary the batch autotuner also times register
+    streaming; whatever it keeps, the state it timed on is restored and the
+    run ends where single handles end."""
+    insts = batch_instances(count=16, seed=4, steps_max=200)
+    data = [instance_ic(i) for i in insts]
+    sims = [w.Wave2D(i.n, i.n, h, i.lam * h, scheme=i.scheme, bc=BC_ZERO, dtype=w.F32)
+            for i, (_, _, h) in zip(insts, data)]
+    steps = [i.steps for i in insts]
+    with w.Batch(sims) as b:
+        b.first_step([d[0] for d in data], [d[1] for d in data])
+        before = [s.get_state() for s in sims]
+        best = b.autotune(steps, probe_steps=16)
+        assert best.kernel in (w.KERNEL_TEMPORAL, w.KERNEL_STREAM) and 1 <= best.temporal_t <= 4
+        after = [s.get_state() for s in sims]
+        for x, y in zip(before, after):
+            assert x[2] == y[2] and np.array_equal(x[1], y[1]) and np.array_equal(x[0], y[0])
+        b.run(steps)
+        for i, (u0, v0, h), s in zip(insts, data, sims):
+            _, uc, _ = s.get_state()
+            ref = alone(w, dict(nx=i.n, ny=i.n, h=h, lam=i.lam, scheme=i.scheme, u0=u0, v0=v0), BC_ZERO, i.steps)
+            assert np.array_equal(uc, ref[1])
+    for s in sims:
         s.close()

@@ -142,3 +142,53 @@ def test_invalid_requests_are_refused(w):
             srv.submit(64, 64, 0.1, 0.05, 10, scheme=7, pulse=(1, 0.5, 0.5, 0.1))
         assert e.value.code == w.ERR_ARG
         srv.drain(10)
+
+
+def test_staging_failure_fails_only_that_rounds_pulse_requests(w):
+    """An allocator hook that refuses the initial-data staging of one pulse
+    request (16 nx ny bytes): that request completes with WAVE2D_ERR_OOM and
+    NaN norms, its levels are not counted, and a request served after it
+    completes normally with the result it has alone."""
+    import ctypes
+    import torch
+    nbad = 16 * 77 * 53                 # staging bytes of the 77 x 53 pulse request
+    refused = []
+
+    def _alloc(nbytes, stream, ctx):
+        if int(nbytes) == nbad:
+            refused.append(int(nbytes))
+            return None
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), 0, int(stream or 0))
+        except Exception:
+            return None
+
+    def _free(ptr, nbytes, stream, ctx):
+        torch.cuda.caching_allocator_delete(int(ptr))
+
+    refs = (w.ALLOC_FN(_alloc), w.FREE_FN(_free))
+    w.check(w.lib().wave2d_set_allocator(refs[0], refs[1], None))
+    try:
+        h = 1.0 / 78
+        with w.Server(budget_bytes=1 << 30, max_resident=8, quantum=16) as srv:
+            srv.submit(77, 53, h, 0.5 * h, 40, scheme=13, pulse=(1.0, 0.5, 0.3, 0.1), tag=1)
+            srv.drain(120)
+            srv.submit(60, 60, h, 0.5 * h, 30, scheme=9, pulse=(1.0, 0.4, 0.4, 0.1), tag=2)
+            srv.drain(120)
+            comps = {int(c.tag): c for c in srv.poll(8)}
+            st = srv.stats()
+    finally:
+        w.use_default_allocator()
+    assert refused, "the hook never saw the staging allocation"
+    bad, good = comps[1], comps[2]
+    assert bad.status == w.ERR_OOM and np.isnan(bad.l2) and np.isnan(bad.linf)
+    assert good.status == 0 and good.k == 31
+    assert st.node_updates == 60 * 60 * 31           # the failed request's levels are not counted
+    n = 60
+    x = (np.arange(n) + 1) * h
+    u0 = np.exp(-((x[None, :] - 0.4) ** 2 + (x[:, None] - 0.4) ** 2) / (2 * 0.1 ** 2))
+    with w.Wave2D(n, n, h, 0.5 * h, scheme=9, bc=BC_ZERO, dtype=w.F32) as sim:
+        sim.first_step(u0, np.zeros_like(u0))
+        sim.step_n(30)
+        l2, linf, _ = sim.error_vs_exact()
+    assert abs(good.l2 - l2) <= 1e-6 * l2 and abs(good.linf - linf) <= 1e-6 * linf
