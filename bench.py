@@ -564,7 +564,8 @@ def measure_batched(w, torch):
             "node_updates": pts, "value": round(pts / batched / 1e9, 2), "unit": "G point-updates/s",
             "ms": round(batched * 1e3, 2), "plain_loop_value": round(pts / plain / 1e9, 2),
             "plain_loop_ms": round(plain * 1e3, 1), "speedup_vs_plain": round(plain / batched, 2),
-            "quantum": best.temporal_t, "tile_h": best.tile_h, "max_rel_norm_diff_vs_plain": agree,
+            "kernel": KSHORT.get(best.kernel), "quantum": best.temporal_t, "tile_h": best.tile_h,
+            "max_rel_norm_diff_vs_plain": agree,
             "timing": "host wall clock around first step + run + norms to host, 3 repetitions"}
 
 

@@ -463,10 +463,16 @@ int build_plan(wave2d_batch* b, const int64_t* steps) {
 // those still running, then one launch per remainder r = steps mod T (r levels)
 // over the instances that have it, each instance at the parity its full
 // launches left it in.
+// Levels per launch of a streaming batch for scheme S: the batch quantum for
+// the 13-point scheme, half as much again (6 for a quantum of 4) for the
+// radius-1 schemes, whose halo columns round up to 8 for depths 5..8 (the
+// single-grid kernel's measurement: 9-point level 13.4 us at T = 4, 11.7 at 6).
+int stream_depth(int S, int Tq) { return S == 13 ? Tq : std::min(6, Tq + Tq / 2); }
+
 int build_stream_plan(wave2d_batch* b, const int64_t* steps) {
     free_plan(b);
     const int n = (int)b->hs.size();
-    const int T = b->Tq, L = b->OH;
+    const int L = b->OH;
     struct Table {
         std::vector<StreamInst> insts;
         std::vector<int> prefix;
@@ -478,6 +484,7 @@ int build_stream_plan(wave2d_batch* b, const int64_t* steps) {
     const int schemes[3] = {13, 9, 5};
     for (int br = 0; br < 3; ++br) {
         const int S = schemes[br];
+        const int T = stream_depth(S, b->Tq);
         std::vector<int> idx;
         for (int i = 0; i < n; ++i)
             if (b->hs[i]->scheme == S && steps[i] > 0) idx.push_back(i);
@@ -560,6 +567,18 @@ int build_stream_plan(wave2d_batch* b, const int64_t* steps) {
 
 template <int S>
 cudaError_t launch_k7(const wave2d_batch::SLaunch& l, int L, cudaStream_t st) {
+    if constexpr (S != 13) {
+        if (l.T == 5) {
+            k7_batch_stream<S, 5><<<l.grid, kStreamWarps * 32, stream_smem_bytes<S, 5>(), st>>>(
+                (const StreamInst*)l.insts, l.prefix, l.n_active, l.q, L);
+            return cudaGetLastError();
+        }
+        if (l.T == 6) {
+            k7_batch_stream<S, 6><<<l.grid, kStreamWarps * 32, stream_smem_bytes<S, 6>(), st>>>(
+                (const StreamInst*)l.insts, l.prefix, l.n_active, l.q, L);
+            return cudaGetLastError();
+        }
+    }
     switch (l.T) {
         case 1: k7_batch_stream<S, 1><<<l.grid, kStreamWarps * 32, stream_smem_bytes<S, 1>(), st>>>(
                     (const StreamInst*)l.insts, l.prefix, l.n_active, l.q, L); break;
@@ -683,7 +702,8 @@ int run_once(wave2d_batch* b, const int64_t* steps) {
     }
     for (int i = 0; i < n; ++i) {
         wave2d* h = b->hs[i];
-        const int64_t nq = (steps[i] + b->Tq - 1) / b->Tq;
+        const int64_t Ti = sm ? stream_depth(h->scheme, b->Tq) : b->Tq;
+        const int64_t nq = (steps[i] + Ti - 1) / Ti;
         if (nq & 1) {
             h->cur ^= 2;
             h->prv ^= 2;
