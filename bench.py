@@ -50,8 +50,8 @@ WORKLOAD = ("9-point + 13-point schemes, FP32 storage, 4096^2 periodic grid, lam
 FP32_OPS = {5: 9, 9: 14, 13: 19}
 
 # Kernel names by WAVE2D_KERNEL_* value (the profiles use the same names).
-KNAME = {1: "k2_simple", 2: "k2_tma", 3: "k3_temporal", 4: "k5_stream"}
-KSHORT = {1: "simple", 2: "tma", 3: "temporal", 4: "stream"}
+KNAME = {1: "k2_simple", 2: "k2_tma", 3: "k3_temporal", 4: "k5_stream", 5: "k2_persist"}
+KSHORT = {1: "simple", 2: "tma", 3: "temporal", 4: "stream", 5: "persistent"}
 
 # DRAM bytes (read + write) of one launch of a kernel at the benchmark size,
 # from an ncu capture of the same kernel source (see the profiles directory),

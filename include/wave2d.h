@@ -154,9 +154,16 @@ enum {
     WAVE2D_KERNEL_SIMPLE = 1,   /* one thread per node, global loads            */
     WAVE2D_KERNEL_TMA = 2,      /* TMA-staged shared-memory tiles, one step      */
     WAVE2D_KERNEL_TEMPORAL = 3, /* TMA tiles advanced T steps in shared memory   */
-    WAVE2D_KERNEL_STREAM = 4    /* T steps per launch with the levels in
+    WAVE2D_KERNEL_STREAM = 4,   /* T steps per launch with the levels in
                                    registers: one warp walks down a strip of 128
                                    columns, halo columns by warp shuffles       */
+    WAVE2D_KERNEL_PERSISTENT = 5 /* every level of a step_n call in one
+                                   cooperative launch (one node per thread per
+                                   pass, a grid barrier between levels, each wait
+                                   bounded): for grids too small to fill the GPU,
+                                   where a launch per level costs more than the
+                                   level; the Section 6 schemes with plain sums,
+                                   any storage type and boundary               */
 };
 /* The two multi-level kernels (TEMPORAL, STREAM) take FP32 handles of the
  * 5-, 9- and 13-point schemes on the zero and periodic boundaries (with
@@ -383,10 +390,12 @@ int wave2d_error_sums(wave2d_t h, const wave2d_exact *ex, int j0, int nrows, int
 
 /* Failure-detection self-test: launch, on the handle's stream, a kernel that
  * waits on an mbarrier nothing ever completes, through the same bounded wait
- * every pipelined kernel uses, with a limit of limit_cycles SM clocks
- * (1 .. 2^31).  The wait gives up and raises the handle's timeout status,
- * which the next synchronising call (wave2d_sync, norms, state) reports as
- * WAVE2D_ERR_TIMEOUT and clears; the GPU stays usable. */
+ * every pipelined kernel uses, and one that waits at the persistent kernel's
+ * grid barrier for an arrival that never comes, each with a limit of
+ * limit_cycles SM clocks (1 .. 2^31).  The waits give up and raise the
+ * handle's timeout status, which the next synchronising call (wave2d_sync,
+ * norms, state) reports as WAVE2D_ERR_TIMEOUT and clears; the GPU stays
+ * usable. */
 int wave2d_selftest_timeout(wave2d_t h, int64_t limit_cycles);
 
 /* Guard-band check of a handle created with WAVE2D_CANARY: *changed receives

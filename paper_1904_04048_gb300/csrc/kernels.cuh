@@ -52,6 +52,7 @@ template <>
 struct St<DT_F32> {
     using V = float;
     __device__ static V ldg(const Level& L, size_t o) { return __ldg((const float*)L.hi + o); }
+    __device__ static V ldcg(const Level& L, size_t o) { return __ldcg((const float*)L.hi + o); }
     __device__ static V ld(const Level& L, size_t o) { return ((const float*)L.hi)[o]; }
     __device__ static void st(const Level& L, size_t o, V v) { ((float*)L.hi)[o] = v; }
     __device__ static double to_d(V v) { return (double)v; }
@@ -61,6 +62,7 @@ template <>
 struct St<DT_F64> {
     using V = double;
     __device__ static V ldg(const Level& L, size_t o) { return __ldg((const double*)L.hi + o); }
+    __device__ static V ldcg(const Level& L, size_t o) { return __ldcg((const double*)L.hi + o); }
     __device__ static V ld(const Level& L, size_t o) { return ((const double*)L.hi)[o]; }
     __device__ static void st(const Level& L, size_t o, V v) { ((double*)L.hi)[o] = v; }
     __device__ static double to_d(V v) { return v; }
@@ -71,6 +73,9 @@ struct St<DT_F32X2> {
     using V = df;
     __device__ static V ldg(const Level& L, size_t o) {
         return {__ldg((const float*)L.hi + o), __ldg((const float*)L.lo + o)};
+    }
+    __device__ static V ldcg(const Level& L, size_t o) {
+        return {__ldcg((const float*)L.hi + o), __ldcg((const float*)L.lo + o)};
     }
     __device__ static V ld(const Level& L, size_t o) {
         return {((const float*)L.hi)[o], ((const float*)L.lo)[o]};
@@ -435,6 +440,93 @@ __global__ void __launch_bounds__(256) k4_norms(Level L, Geo g, ExactTab ex, Red
             error_terms(T::to_d(T::ld(L, off(g, i, j))), exact_at(ex, i, j), s0, s1, m0, m1,
                         rd.status);
     reduce_finalize<256>(s0, s1, m0, m1, rd);
+}
+
+// ---------------------------------------------------------------------------
+// K2 persistent: every level of a run in one cooperative launch, for grids
+// too small to fill the GPU, where a launch per level costs more than the
+// level itself.  Blocks stride over the nodes of a level (one node per thread
+// per pass, as in k2_simple: the same per-node arithmetic, in place over
+// u^{k-1}), then meet at a grid barrier before the next level.  Neighbours are
+// read through L2 (ld.global.cg): another SM wrote them a level ago, and L1 is
+// not coherent between SMs.
+// ---------------------------------------------------------------------------
+
+// Grid barrier: a 64-bit arrival count that only grows; barrier e of a launch
+// completes when every block has arrived e + 1 times.  The wait is bounded
+// (limit SM clocks): on expiry the block raises STATUS_TIMEOUT and returns
+// false, and the kernel ends (the other blocks then expire at their next
+// barrier).  Needs every block resident: a cooperative launch.
+__device__ __forceinline__ bool grid_barrier(unsigned long long* arrived, unsigned long long target, int* status,
+                                            long long limit) {
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        ok = 1;
+        __threadfence();  // this block's stores of the level before the arrival
+        atomicAdd(arrived, 1ull);
+        const long long t0 = clock64();
+        while (*(volatile unsigned long long*)arrived < target) {
+            if (clock64() - t0 > limit) {
+                atomicOr(status, STATUS_TIMEOUT);
+                ok = 0;
+                break;
+            }
+            __nanosleep(32);
+        }
+        __threadfence();  // the other blocks' stores before this block's next reads
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+template <int DT, int S, int BCM>
+__global__ void __launch_bounds__(256) k2_persist(Level A, Level B, Geo g, Coef3<typename St<DT>::V> a,
+                                                  int n_levels, unsigned long long* arrived, int* status, int gw,
+                                                  long long limit) {
+    using T = St<DT>;
+    using V = typename T::V;
+    const long long nn = (long long)g.nx * g.ny;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const size_t P = (size_t)g.pitch;
+    for (int l = 0; l < n_levels; ++l) {
+        const Level cur = (l & 1) ? B : A;  // u^k
+        const Level nxt = (l & 1) ? A : B;  // u^{k-1}, overwritten with u^{k+1}
+        for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < nn; q += stride) {
+            const int i = (int)(q % g.nx), j = (int)(q / g.nx);
+            const size_t o = off(g, i, j);
+            Nbr<V> u;
+            u.c = T::ldcg(cur, o);
+            u.e = T::ldcg(cur, o + 1);
+            u.w = T::ldcg(cur, o - 1);
+            u.n = T::ldcg(cur, o + P);
+            u.s = T::ldcg(cur, o - P);
+            if constexpr (S >= 9) {
+                u.ne = T::ldcg(cur, o + P + 1);
+                u.nw = T::ldcg(cur, o + P - 1);
+                u.se = T::ldcg(cur, o - P + 1);
+                u.sw = T::ldcg(cur, o - P - 1);
+            }
+            if constexpr (S == 13) {
+                u.ee = T::ldcg(cur, o + 2);
+                u.ww = T::ldcg(cur, o - 2);
+                u.nn = T::ldcg(cur, o + 2 * P);
+                u.ss = T::ldcg(cur, o - 2 * P);
+            }
+            const V r = two_step_update<S>(u, T::ldcg(nxt, o), a);
+            T::st(nxt, o, r);
+            if (BCM != BCM_ZERO) write_images_bc<DT, BCM>(nxt, g, i, j, r, gw);
+        }
+        if (l + 1 < n_levels && !grid_barrier(arrived, (unsigned long long)(l + 1) * gridDim.x, status, limit))
+            return;
+    }
+}
+
+// Self-test of the grid barrier's bounded wait: one block waits for arrivals
+// that never come (target 2, one arrival), gives up after `limit` clocks and
+// raises STATUS_TIMEOUT.
+static __global__ void k_selftest_grid_wait(unsigned long long* arrived, int* status, long long limit) {
+    grid_barrier(arrived, 2ull, status, limit);
 }
 
 // Norms of the difference of two fields of the same grid (any storage types),

@@ -81,7 +81,7 @@ __device__ __forceinline__ V class_delta(const F& u, V c) {
             const V t = vadd(vadd(u(q2, q1), u(-q2, -q1)), vadd(u(-q1, q2), u(q1, -q2)));
             s = vadd(s, t);
         }
-        return vadd(s, vscale(c, -(float)chain_nodes(C)));
+        return vadd_scaled(s, c, -(float)chain_nodes(C));
     }
 }
 
@@ -104,7 +104,7 @@ __device__ __forceinline__ V lambda_chain(const F& u, V c, const CoefN<V, NC>& a
 template <int NC, bool DIFF = false, typename V, typename F>
 __device__ __forceinline__ V two_step_chain(const F& u, V c, V prev, const CoefN<V, NC>& a) {
     const V L = lambda_chain<NC, DIFF>(u, c, a);
-    const V base = vsub(vscale(c, 2.0f), prev);
+    const V base = vtwo_minus(c, prev);
     return vadd(base, L);
 }
 

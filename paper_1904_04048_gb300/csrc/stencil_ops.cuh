@@ -86,6 +86,18 @@ __device__ __forceinline__ float vsub(float a, float b) { return __fsub_rn(a, b)
 __device__ __forceinline__ double vsub(double a, double b) { return __dsub_rn(a, b); }
 __device__ __forceinline__ df vsub(df a, df b) { return df_add(a, df_neg(b)); }
 
+// x + s a for a power-of-two s (s a exact): for float and double one fused
+// multiply-add, which rounds once exactly as the sum x + (s a) does; for
+// double-float the sum itself, in that operand order.
+__device__ __forceinline__ float vadd_scaled(float x, float a, float s) { return __fmaf_rn(a, s, x); }
+__device__ __forceinline__ double vadd_scaled(double x, double a, float s) { return __fma_rn(a, (double)s, x); }
+__device__ __forceinline__ df vadd_scaled(df x, df a, float s) { return df_add(x, df_scale(a, s)); }
+
+// 2 c - p: one rounding (2 c is exact); the double-float form subtracts.
+__device__ __forceinline__ float vtwo_minus(float c, float p) { return __fmaf_rn(c, 2.0f, -p); }
+__device__ __forceinline__ double vtwo_minus(double c, double p) { return __fma_rn(c, 2.0, -p); }
+__device__ __forceinline__ df vtwo_minus(df c, df p) { return df_add(df_scale(c, 2.0f), df_neg(p)); }
+
 template <typename V>
 struct Coef3 {
     V a10, a11, a20;
@@ -98,17 +110,18 @@ struct Nbr {
     V c, e, w, n, s, ne, nw, se, sw, ee, ww, nn, ss;
 };
 
+// Each class sum adds its -4 u_ij term last (vadd_scaled: one rounding, the
+// same as adding the exact product -4 u_ij).
 template <int S, typename V>
 __device__ __forceinline__ V lambda_sum(const Nbr<V>& u, const Coef3<V>& a) {
-    V m4c = vscale(u.c, -4.0f);
-    V d10 = vadd(vadd(vadd(u.e, u.w), vadd(u.n, u.s)), m4c);
+    V d10 = vadd_scaled(vadd(vadd(u.e, u.w), vadd(u.n, u.s)), u.c, -4.0f);
     V L = vmul(a.a10, d10);
     if constexpr (S >= 9) {
-        V d11 = vadd(vadd(vadd(u.ne, u.sw), vadd(u.nw, u.se)), m4c);
+        V d11 = vadd_scaled(vadd(vadd(u.ne, u.sw), vadd(u.nw, u.se)), u.c, -4.0f);
         L = vfma(a.a11, d11, L);
     }
     if constexpr (S == 13) {
-        V d20 = vadd(vadd(vadd(u.ee, u.ww), vadd(u.nn, u.ss)), m4c);
+        V d20 = vadd_scaled(vadd(vadd(u.ee, u.ww), vadd(u.nn, u.ss)), u.c, -4.0f);
         L = vfma(a.a20, d20, L);
     }
     return L;
@@ -123,7 +136,7 @@ __device__ __forceinline__ V lambda_sum(const Nbr<V>& u, const Coef3<V>& a) {
 template <int S, typename V>
 __device__ __forceinline__ V two_step_update(const Nbr<V>& u, V prev, const Coef3<V>& a) {
     V L = lambda_sum<S>(u, a);
-    V base = vsub(vscale(u.c, 2.0f), prev);
+    V base = vtwo_minus(u.c, prev);
     return vadd(base, L);
 }
 

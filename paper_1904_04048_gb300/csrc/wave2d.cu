@@ -464,6 +464,50 @@ static int launch_temporal(wave2d* h) {
 
 // Advance by one launch: T levels for the temporal kernel when at least T
 // remain, else one level.  Returns the number of levels advanced (< 0: error).
+// All n levels in one cooperative launch of k2_persist (grid barrier between
+// levels), blocks capped at the number that can be resident at once.
+template <int DT, int S, int BCM>
+static int launch_persist_t(wave2d* h, int n) {
+    auto kern = k2_persist<DT, S, BCM>;
+    static int per_sm = -1;  // resident blocks of 256 threads per SM for this instantiation
+    if (per_sm < 0) {
+        int v = 0;
+        W2D_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, kern, 256, 0), "occupancy query");
+        per_sm = std::max(1, v);
+    }
+    const long long nn = (long long)h->nx * h->ny;
+    const int blocks = (int)std::max<long long>(1, std::min<long long>((nn + 255) / 256, (long long)per_sm * h->num_sms));
+    unsigned long long* arrived = reinterpret_cast<unsigned long long*>(reinterpret_cast<char*>(h->counter) + 128);
+    W2D_CUDA(cudaMemsetAsync(arrived, 0, sizeof(unsigned long long), h->stream), "barrier reset");
+    Level A = h->level(h->cur), B = h->level(h->prv);
+    Geo g = h->geo();
+    Coef3<typename St<DT>::V> a = coef_as<typename St<DT>::V>(h->a);
+    int* status = h->status;
+    int gw = h->gw;
+    long long limit = kWaitLimitCycles;
+    void* args[] = {&A, &B, &g, &a, &n, &arrived, &status, &gw, &limit};
+    W2D_CUDA(cudaLaunchCooperativeKernel((const void*)kern, dim3(blocks), dim3(256), args, 0, h->stream),
+             "persistent kernel launch");
+    W2D_LAUNCHED("persistent kernel launch");
+    return WAVE2D_OK;
+}
+
+static int launch_persist(wave2d* h, int n) {
+    int rc = WAVE2D_OK;
+    dispatch_dt(h->dtype, [&](auto DTc) {
+        dispatch_s(h->scheme, [&](auto Sc) {
+            constexpr int DT = decltype(DTc)::value, S = decltype(Sc)::value;
+            if (h->bc == WAVE2D_BC_PERIODIC) rc = launch_persist_t<DT, S, BCM_PERIODIC>(h, n);
+            else if (h->bc == WAVE2D_BC_ODD) rc = launch_persist_t<DT, S, BCM_ODD>(h, n);
+            else rc = launch_persist_t<DT, S, BCM_ZERO>(h, n);
+        });
+    });
+    if (rc != WAVE2D_OK) return rc;
+    if (n & 1) std::swap(h->cur, h->prv);
+    h->k += n;
+    return WAVE2D_OK;
+}
+
 static int launch_block(wave2d* h, int64_t remaining) {
     int rc;
     if (h->kernel == WAVE2D_KERNEL_STREAM && remaining >= h->temporal_t) {
@@ -533,6 +577,8 @@ static int select_kernel(wave2d* h) {
                                                      : WAVE2D_KERNEL_TMA;
     }
     if (is_multilevel(want) && (h->dtype != DT_F32 || !multilevel_ok(h))) want = WAVE2D_KERNEL_TMA;
+    if (want == WAVE2D_KERNEL_PERSISTENT && (h->nclass > 0 || h->diff_sums || h->diff_form))
+        want = WAVE2D_KERNEL_SIMPLE;
     if (want == WAVE2D_KERNEL_TMA && h->dtype == DT_F32X2) want = WAVE2D_KERNEL_SIMPLE;
     if ((want == WAVE2D_KERNEL_TMA || is_multilevel(want)) && !h->tma_ready) {
         int rc = prepare_tma(h);  // the multi-level kernels finish runs with single TMA steps
@@ -896,8 +942,10 @@ void wave2d_destroy(wave2d_t h) { release_handle(h); }
 
 int wave2d_set_tuning(wave2d_t h, const wave2d_tune* tune) {
     if (!h || !tune) return set_error(WAVE2D_ERR_ARG, "null argument");
-    if (tune->kernel < 0 || tune->kernel > WAVE2D_KERNEL_STREAM)
+    if (tune->kernel < 0 || tune->kernel > WAVE2D_KERNEL_PERSISTENT)
         return set_error(WAVE2D_ERR_ARG, "unknown kernel %d", tune->kernel);
+    if (tune->kernel == WAVE2D_KERNEL_PERSISTENT && (h->nclass > 0 || h->diff_sums || h->diff_form))
+        return set_error(WAVE2D_ERR_ARG, "the persistent kernel covers the 5-, 9- and 13-point schemes with plain sums");
     if (tune->kernel == WAVE2D_KERNEL_TMA && h->dtype == WAVE2D_F32X2)
         return set_error(WAVE2D_ERR_ARG, "the TMA kernel supports F32 and F64 storage only");
     const bool multi = is_multilevel(tune->kernel);
@@ -1021,6 +1069,15 @@ int wave2d_step_n(wave2d_t h, int64_t n) {
             h->k += 1;
         }
         return WAVE2D_OK;
+    }
+    if (h->kernel == WAVE2D_KERNEL_PERSISTENT) {
+        int rc = stream_fresh_rings(h);
+        while (rc == WAVE2D_OK && n > 0) {
+            const int m = (int)std::min<int64_t>(n, 1 << 30);
+            rc = launch_persist(h, m);
+            n -= m;
+        }
+        return rc;
     }
     if (want_graph(h, n)) {
         int rc = run_graph(h, n);
@@ -1373,6 +1430,8 @@ int wave2d_autotune(wave2d_t h, int64_t steps, wave2d_tune* best) {
         t.ctas_per_sm = per_sm;
         cands.push_back(t);
     };
+    const bool persist_ok = h->nclass == 0 && !h->diff_sums && !h->diff_form &&
+                            (int64_t)h->nx * h->ny <= (int64_t(1) << 20);
     if (h->dtype == WAVE2D_F32 && !multilevel_ok(h)) {
         add(WAVE2D_KERNEL_TMA, 0, 0, 1);
         add(WAVE2D_KERNEL_TMA, 0, 0, 2);
@@ -1391,6 +1450,7 @@ int wave2d_autotune(wave2d_t h, int64_t steps, wave2d_tune* best) {
     } else {
         add(WAVE2D_KERNEL_SIMPLE, 0, 0, 0);
     }
+    if (persist_ok) add(WAVE2D_KERNEL_PERSISTENT, 0, 0, 0);
     if (h->tracking || cands.size() == 1) {
         h->tune = cands[0];
         int rc = select_kernel(h);
@@ -1473,6 +1533,12 @@ int wave2d_selftest_timeout(wave2d_t h, int64_t limit_cycles) {
     if (limit_cycles < 1 || limit_cycles > (1LL << 31))
         return set_error(WAVE2D_ERR_ARG, "limit must be 1 .. 2^31 cycles");
     k_selftest_wait<<<1, 32, 0, h->stream>>>(h->status, (long long)limit_cycles);
+    W2D_LAUNCHED("self-test kernel launch");
+    // the persistent kernel's grid barrier: one block waiting for an arrival
+    // that never comes
+    unsigned long long* arrived = reinterpret_cast<unsigned long long*>(reinterpret_cast<char*>(h->counter) + 128);
+    W2D_CUDA(cudaMemsetAsync(arrived, 0, sizeof(unsigned long long), h->stream), "barrier reset");
+    k_selftest_grid_wait<<<1, 32, 0, h->stream>>>(arrived, h->status, (long long)limit_cycles);
     W2D_LAUNCHED("self-test kernel launch");
     return WAVE2D_OK;
 }

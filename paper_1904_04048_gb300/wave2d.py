@@ -23,7 +23,7 @@ BC_ZERO, BC_PERIODIC, BC_ODD = 0, 1, 2
 F64, F32, F32X2 = 0, 1, 2
 ALLOW_UNSTABLE, CONVENTIONAL, DIFF_SUMS, DIFF_FORM, CANARY = 1, 2, 4, 8, 16
 EXACT_NONE, EXACT_STANDING, EXACT_PLANE = 0, 1, 2
-KERNEL_AUTO, KERNEL_SIMPLE, KERNEL_TMA, KERNEL_TEMPORAL, KERNEL_STREAM = 0, 1, 2, 3, 4
+KERNEL_AUTO, KERNEL_SIMPLE, KERNEL_TMA, KERNEL_TEMPORAL, KERNEL_STREAM, KERNEL_PERSISTENT = 0, 1, 2, 3, 4, 5
 
 _NAMES = {ERR_ARG: "ERR_ARG", ERR_UNSTABLE: "ERR_UNSTABLE", ERR_OOM: "ERR_OOM", ERR_CUDA: "ERR_CUDA",
           ERR_NONFINITE: "ERR_NONFINITE", ERR_TIMEOUT: "ERR_TIMEOUT", ERR_STATE: "ERR_STATE"}

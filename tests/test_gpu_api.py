@@ -210,7 +210,7 @@ def test_stream_tuning_is_validated(w):
                 sim.set_tuning(kernel=w.KERNEL_STREAM, **bad)
             assert e.value.code == w.ERR_ARG
         with pytest.raises(w.Wave2DError) as e:
-            sim.set_tuning(kernel=5)
+            sim.set_tuning(kernel=6)   # no such kernel
         assert e.value.code == w.ERR_ARG
         for rows in (0, 8, 37, 4096):
             sim.set_tuning(kernel=w.KERNEL_STREAM, temporal_t=3, tile_h=rows)
