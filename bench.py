@@ -508,7 +508,8 @@ def run_ours(args, rank, world, local_rank):
         line["batched"] = measure_batched(w, torch)
         line["served"] = measure_served(w, torch)
         line["derived_schemes"] = measure_derived(w, torch, u0, v0, peak)
-        line["fp32_difference_sums"] = measure_diff_sums(w, torch, u0, v0, peak)
+        plain_us = {s: line["per_scheme_ms_per_level"][str(s)] * 1e3 for s in SCHEMES}
+        line["fp32_difference_sums"] = measure_diff_sums(w, torch, u0, v0, peak, plain_us)
         if args.precision != "off":
             line["precision"] = measure_precision(w, torch, args.precision)
     if world == 1 and not args.no_cpu_baseline:
@@ -810,13 +811,16 @@ def measure_derived(w, torch, u0, v0, peak):
     return out
 
 
-def measure_diff_sums(w, torch, u0, v0, peak):
+def measure_diff_sums(w, torch, u0, v0, peak, plain_us=None):
     """The 9- and 13-point schemes in FP32 with WAVE2D_DIFF_SUMS (stencil sums
-    from differences to the centre; 12 B per node-update) and with
-    WAVE2D_DIFF_FORM (levels kept as u^k and d^k = u^k - u^{k-1}; 16 B per
-    node-update) on the benchmark grid and inputs: autotuned two-step kernel,
-    200 levels timed with CUDA events after 20 warm-up levels; HBM roofline
-    at the algorithmic bytes."""
+    from differences to the centre) and with WAVE2D_DIFF_FORM (levels kept as
+    u^k and d^k = u^k - u^{k-1}) on the benchmark grid and inputs: autotuned
+    two-step kernel, 200 levels timed with CUDA events after 20 warm-up
+    levels.  Algorithmic bytes per node-update: 12 (sums) or 16 (form) for a
+    one-level kernel, 16 / T for the streaming kernel (two planes read, two
+    written per launch of T levels), which is bound by the FP32 pipe, not
+    HBM: ``vs_plain`` is the time per level over the plain two-step's on the
+    same grid (``plain_us``, from the main measurement)."""
     from initial_data import BC_PERIODIC, LAMBDA_MAX
     out = {}
     h = 1.0 / N
@@ -837,15 +841,22 @@ def measure_diff_sums(w, torch, u0, v0, peak):
             e1.record(stream)
             e1.synchronize()
             sec = e0.elapsed_time(e1) / 1e3 / levels
-        out[f"{name}_{scheme}"] = {"us_per_level": round(sec * 1e6, 2), "value": round(N * N / sec / 1e9, 1),
-                                   "unit": "G point-updates/s",
-                                   "kernel": KSHORT.get(best.kernel),
-                                   "bytes_per_node_update": bpn,
-                                   "hbm_frac": round(bpn * N * N / sec / 1e9 / peak, 3)}
+            info = sim.info()
+        T = info.temporal_t if info.kernel == w.KERNEL_STREAM else 1
+        bytes_per = bpn if T == 1 else 16 / T
+        row = {"us_per_level": round(sec * 1e6, 2), "value": round(N * N / sec / 1e9, 1),
+               "unit": "G point-updates/s", "kernel": KSHORT.get(info.kernel), "levels_per_launch": T,
+               "strip_rows": best.tile_h if T > 1 else None,
+               "bytes_per_node_update": round(bytes_per, 3),
+               "hbm_frac": round(bytes_per * N * N / sec / 1e9 / peak, 3)}
+        if plain_us and plain_us.get(scheme):
+            row["vs_plain"] = round(sec * 1e6 / plain_us[scheme], 3)
+        out[f"{name}_{scheme}"] = row
     return out
 
 
-def profile_case(kernel: str, scheme: int, segment: int = 28, tile_h: int = 32, depth: int = 4):
+def profile_case(kernel: str, scheme: int, segment: int = 28, tile_h: int = 32, depth: int = 4,
+                 mode: str = "plain"):
     """A short run of one kernel at the benchmark size, for profiler captures:
     the first step, then a few launches of the named kernel on the
     benchmark's inputs (no timing, no JSON line).  4096^2 FP32 holds about
@@ -863,7 +874,8 @@ def profile_case(kernel: str, scheme: int, segment: int = 28, tile_h: int = 32, 
         lam = 0.9 * w.scheme_lambda_max(scheme)
     else:
         lam = 0.9 * LAMBDA_MAX[scheme]
-    with w.Wave2D(N, N, h, lam * h, scheme=scheme, bc=BC_PERIODIC, dtype=w.F32) as sim:
+    flags = {"plain": 0, "sums": w.DIFF_SUMS, "form": w.DIFF_FORM}[mode]
+    with w.Wave2D(N, N, h, lam * h, scheme=scheme, bc=BC_PERIODIC, dtype=w.F32, flags=flags) as sim:
         if kernel in ("k2_tma", "kc2_tma"):
             sim.set_tuning(kernel=w.KERNEL_TMA, use_graph=0)
             levels = 4
@@ -876,7 +888,8 @@ def profile_case(kernel: str, scheme: int, segment: int = 28, tile_h: int = 32, 
         sim.first_step(u0, v0)
         sim.step_n(levels)
         sim.sync()
-        print(f"profile case {kernel}, {sim.info().n_points} points, {N}^2: {levels} levels after the first step")
+        print(f"profile case {kernel} ({mode}), {sim.info().n_points} points, {N}^2: {levels} levels after the "
+              f"first step")
 
 
 def run_reference(args, rank):
@@ -935,10 +948,12 @@ def main():
     ap.add_argument("--profile-segment", type=int, default=28, help="derived scheme for kc2_tma")
     ap.add_argument("--profile-tile", type=int, default=32, help="rows per tile or strip (k3_temporal, k5_stream)")
     ap.add_argument("--profile-depth", type=int, default=4, help="levels per launch of k5_stream")
+    ap.add_argument("--profile-mode", choices=["plain", "sums", "form"], default="plain",
+                    help="storage and arithmetic: plain sums, WAVE2D_DIFF_SUMS or WAVE2D_DIFF_FORM")
     args = ap.parse_args()
     if args.profile_case:
         profile_case(args.profile_case, args.profile_scheme, args.profile_segment, args.profile_tile,
-                     args.profile_depth)
+                     args.profile_depth, args.profile_mode)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -73,8 +73,8 @@ inline void dispatch_bcm(int bc, Fn&& fn) {
 // chain_f32x2.cu, so the three compile in parallel).
 template <int DT>
 int chain_first_step_dt(wave2d* h, const double* du0, const double* dv0, const ExactTab& ex, const Reduce& rd) {
-    // u^0 -> plane 1 (u^{k-1}), u^1 -> plane 0; difference form: d^1 -> plane 2
-    const Level L0 = h->level(h->diff_form ? 2 : 1), L1 = h->level(0);
+    // u^0 -> plane 1 (u^{k-1}), u^1 -> plane 0; difference form: d^1 -> plane dpl
+    const Level L0 = h->level(h->diff_form ? h->dpl : 1), L1 = h->level(0);
     dispatch_nc(h->nclass, [&](auto NCc) {
         constexpr int NC = decltype(NCc)::value;
         const CoefN<double, NC> ahalf = coef_n<double, NC>(h->ca, 0.5), b = coef_n<double, NC>(h->cb);
@@ -97,7 +97,7 @@ template <int DT>
 int chain_simple_step_dt(wave2d* h, bool track, const ExactTab& ex, const Reduce& rd) {
     using V = typename St<DT>::V;
     const Level cur = h->level(h->cur), nxt = h->level(h->prv);
-    const Level dpl = h->diff_form ? h->level(2) : Level{nullptr, nullptr};
+    const Level dpl = h->diff_form ? h->level(h->dpl) : Level{nullptr, nullptr};
     // difference sums exist for FP32 and FP64 storage, the difference form
     // (which implies them) for FP32
     const int mode = (h->diff_form && DT == DT_F32) ? 2 : (h->diff_sums && DT != DT_F32X2) ? 1 : 0;

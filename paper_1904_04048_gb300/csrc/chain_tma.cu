@@ -45,8 +45,8 @@ int launch_tma(wave2d* h) {
     if (per_sm <= 0) per_sm = (2.0 * (double)h->plane_bytes <= 1.25 * (double)h->l2_bytes) ? occ : 1;
     per_sm = std::max(1, std::min(per_sm, occ));
     const int grid = std::min(n_tiles, per_sm * h->num_sms);
-    // difference form: the second staged box is d^k (plane 2), updated in place
-    const int second = DFORM ? 2 : h->prv;
+    // difference form: the second staged box is d^k (plane dpl), updated in place
+    const int second = DFORM ? h->dpl : h->prv;
     kern<<<grid, kNW * 32, smem, h->stream>>>(h->tm_cur[h->cur], h->tm_prev[second],
                                               reinterpret_cast<T*>(h->hi[h->prv]), h->geo(),
                                               coef_n<T, NC>(h->ca), tiles_x, n_tiles, h->gw, h->status,

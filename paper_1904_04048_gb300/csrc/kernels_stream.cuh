@@ -145,6 +145,89 @@ __device__ __forceinline__ void stream_level(const float (&lv)[WIN][4], const fl
     }
 }
 
+// Storage and arithmetic modes of the streaming kernel.
+constexpr int kStreamPlain = 0;  // u^k, u^{k-1}; sums of the nodes (stencil_ops.cuh)
+constexpr int kStreamSums = 1;   // WAVE2D_DIFF_SUMS: u^k, u^{k-1}; sums of differences to the centre
+constexpr int kStreamForm = 2;   // WAVE2D_DIFF_FORM: u^k, d^k = u^k - u^{k-1}; sums of differences
+
+// Difference sums: one level on one row from the rows of u^{t-1} (as
+// stream_level), every class sum formed from the differences to the centre,
+// and the row `p` of the second input:
+//   FORM (difference form): p = d^{t-1} = u^{t-1} - u^{t-2};
+//     d^t = d^{t-1} + Lambda(u^{t-1}),  u^t = u^{t-1} + d^t;
+//   otherwise: p = u^{t-2};  u^t = (2 u^{t-1} - u^{t-2}) + Lambda(u^{t-1}).
+// The operations, their order and rounding are those of two_step_chain_dform
+// and two_step_chain with difference sums (stencil_chain.cuh), lane by lane,
+// so the results equal the one-level kernels of those modes bit for bit.
+__device__ __forceinline__ float dsub(float x, float c) { return __fsub_rn(x, c); }
+
+template <int S, int WIN, int CS, bool FORM>
+__device__ __forceinline__ void stream_level_df(const float (&lv)[WIN][4], const float (&dprev)[4],
+                                                float (&uout)[4], float (&dout)[4], const Coef3<float>& a,
+                                                f2x a10x2, f2x a11x2, f2x a20x2) {
+    constexpr int UP = (CS + 1) % WIN, DN = (CS + WIN - 1) % WIN;
+    if constexpr (S == 5) {
+        float c8[8];
+        lane_row<1>(lv[CS], c8);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const float c = c8[e + 2];
+            const float s0 = __fadd_rn(__fadd_rn(dsub(c8[e + 3], c), dsub(c8[e + 1], c)),
+                                       __fadd_rn(dsub(lv[UP][e], c), dsub(lv[DN][e], c)));
+            const float L = __fmul_rn(a.a10, s0);
+            if constexpr (FORM) {
+                dout[e] = __fadd_rn(dprev[e], L);
+                uout[e] = __fadd_rn(c, dout[e]);
+            } else {
+                uout[e] = __fadd_rn(__fmaf_rn(c, 2.0f, -dprev[e]), L);
+            }
+        }
+    } else {
+        constexpr int UP2 = (CS + 2) % WIN, DN2 = (CS + 2 * WIN - 2) % WIN;  // 13-point only
+        float c[8], up[8], dn[8], up2[8], dn2[8];
+        lane_row<(S == 13) ? 2 : 1>(lv[CS], c);
+        lane_row<1>(lv[UP], up);
+        lane_row<1>(lv[DN], dn);
+        lane_row<0>(lv[S == 13 ? UP2 : UP], up2);
+        lane_row<0>(lv[S == 13 ? DN2 : DN], dn2);
+        const f2x m1 = pk2(-1.0f, -1.0f);
+#pragma unroll
+        for (int e = 0; e < 4; e += 2) {
+            const f2x cc = pk2(c[e + 2], c[e + 3]);
+            // pairs that start at an odd column: two scalar differences; even
+            // pairs: x - c as one packed FMA x + c * (-1), the same rounding
+            const f2x de = pk2(dsub(c[e + 3], c[e + 2]), dsub(c[e + 4], c[e + 3]));
+            const f2x dw = pk2(dsub(c[e + 1], c[e + 2]), dsub(c[e + 2], c[e + 3]));
+            const f2x dnn = fma2(cc, m1, pk2(up[e + 2], up[e + 3]));
+            const f2x dss = fma2(cc, m1, pk2(dn[e + 2], dn[e + 3]));
+            const f2x s0 = add2(add2(de, dw), add2(dnn, dss));
+            f2x L = mul2(a10x2, s0);
+            const f2x dne = pk2(dsub(up[e + 3], c[e + 2]), dsub(up[e + 4], c[e + 3]));
+            const f2x dsw = pk2(dsub(dn[e + 1], c[e + 2]), dsub(dn[e + 2], c[e + 3]));
+            const f2x dnw = pk2(dsub(up[e + 1], c[e + 2]), dsub(up[e + 2], c[e + 3]));
+            const f2x dse = pk2(dsub(dn[e + 3], c[e + 2]), dsub(dn[e + 4], c[e + 3]));
+            const f2x s1 = add2(add2(dne, dsw), add2(dnw, dse));
+            L = fma2(a11x2, s1, L);
+            if constexpr (S == 13) {
+                const f2x dee = fma2(cc, m1, pk2(c[e + 4], c[e + 5]));
+                const f2x dww = fma2(cc, m1, pk2(c[e], c[e + 1]));
+                const f2x dn2n = fma2(cc, m1, pk2(up2[e + 2], up2[e + 3]));
+                const f2x ds2s = fma2(cc, m1, pk2(dn2[e + 2], dn2[e + 3]));
+                const f2x s2 = add2(add2(dee, dww), add2(dn2n, ds2s));
+                L = fma2(a20x2, s2, L);
+            }
+            if constexpr (FORM) {
+                const f2x dnew = add2(pk2(dprev[e], dprev[e + 1]), L);
+                upk2(dnew, dout[e], dout[e + 1]);
+                upk2(add2(cc, dnew), uout[e], uout[e + 1]);
+            } else {  // 2c - p as one FMA, then + Lambda
+                const f2x base = fma2(cc, pk2(2.0f, 2.0f), pk2(-dprev[e], -dprev[e + 1]));
+                upk2(add2(base, L), uout[e], uout[e + 1]);
+            }
+        }
+    }
+}
+
 template <typename F, int... I>
 __device__ __forceinline__ void static_for_impl(F& f, std::integer_sequence<int, I...>) {
     (f(std::integral_constant<int, I>{}), ...);
@@ -226,12 +309,13 @@ __device__ __forceinline__ void stream_store_checked(const StreamWarp& w, const 
 // first T (D + R) steps) and steps past the end are skipped by warp-uniform
 // branches, and interior strips (full vectors, rows inside the grid) store
 // with predicated instructions.
-template <int S, bool PER, int T, bool WRAP>
+template <int S, bool PER, int T, bool WRAP, int M>
 __device__ __forceinline__ void stream_group(const StreamWarp& w, const Geo& g, const Coef3<float>& a, f2x a10x2,
                                              f2x a11x2, f2x a20x2, float (&q)[T][StreamCfg<S, T>::WIN][4],
-                                             int base) {
+                                             float (&qd)[T][StreamCfg<S, T>::WIN][4], int base) {
     using C = StreamCfg<S, T>;
     constexpr int R = C::R, D = C::D, WIN = C::WIN, NB = C::NB, PF = C::PF;
+    constexpr bool DF = M == kStreamForm;
     static_for<WIN>([&](auto sc) {
         constexpr int s = decltype(sc)::value;
         const int step = base + s;
@@ -243,29 +327,50 @@ __device__ __forceinline__ void stream_group(const StreamWarp& w, const Geo& g, 
         float pm[4];
         f4_to(src[32], pm);
         stream_issue<D, NB, WRAP>(w, g, step + PF);
-        float top[4];  // level T on row rho - T D
+        float top[4], dtop[4];  // level T on row rho - T D (and, difference form, its d)
         static_for<T>([&](auto tc) {
             constexpr int t = decltype(tc)::value + 1;
             constexpr int cs = ((s - t * D) % WIN + 2 * WIN) % WIN;  // slot of row rho - tD
             if (step < t * (D + R)) return;  // level t on row rho - tD has no valid inputs yet
-            float out[4];
-            if constexpr (t == 1) stream_level<S, WIN, cs>(q[0], pm, out, a, a10x2, a11x2, a20x2);
-            else stream_level<S, WIN, cs>(q[t - 1], q[t >= 2 ? t - 2 : 0][cs], out, a, a10x2, a11x2, a20x2);
+            float out[4], dout[4];
+            if constexpr (DF) {
+                // the row's d^{t-1}: loaded with the step for t = 1, else kept
+                // since level t-1 computed this row D steps ago
+                if constexpr (t == 1) stream_level_df<S, WIN, cs, true>(q[0], pm, out, dout, a, a10x2, a11x2, a20x2);
+                else stream_level_df<S, WIN, cs, true>(q[t - 1], qd[t >= 2 ? t - 1 : 0][cs], out, dout, a, a10x2,
+                                                       a11x2, a20x2);
+            } else if constexpr (M == kStreamSums) {
+                if constexpr (t == 1) stream_level_df<S, WIN, cs, false>(q[0], pm, out, dout, a, a10x2, a11x2, a20x2);
+                else stream_level_df<S, WIN, cs, false>(q[t - 1], q[t >= 2 ? t - 2 : 0][cs], out, dout, a, a10x2,
+                                                        a11x2, a20x2);
+            } else {
+                if constexpr (t == 1) stream_level<S, WIN, cs>(q[0], pm, out, a, a10x2, a11x2, a20x2);
+                else stream_level<S, WIN, cs>(q[t - 1], q[t >= 2 ? t - 2 : 0][cs], out, a, a10x2, a11x2, a20x2);
+            }
             if constexpr (!PER) {
                 const int r = rho - t * D;
                 const bool rowin = r >= 0 && r < g.ny;
 #pragma unroll
-                for (int e = 0; e < 4; ++e) out[e] = (rowin && w.colin[e]) ? out[e] : 0.0f;
+                for (int e = 0; e < 4; ++e) {
+                    out[e] = (rowin && w.colin[e]) ? out[e] : 0.0f;
+                    if constexpr (DF) dout[e] = (rowin && w.colin[e]) ? dout[e] : 0.0f;
+                }
             }
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
-                if constexpr (t < T) q[t < T ? t : 0][cs][e] = out[e];
-                else top[e] = out[e];
+                if constexpr (t < T) {
+                    q[t < T ? t : 0][cs][e] = out[e];
+                    if constexpr (DF) qd[t < T ? t : 0][cs][e] = dout[e];
+                } else {
+                    top[e] = out[e];
+                    if constexpr (DF) dtop[e] = dout[e];
+                }
             }
         });
         if (step < T * (D + R)) return;  // no output row yet
         constexpr int ps = ((s - T * D) % WIN + 2 * WIN) % WIN;
-        const float(&pv)[4] = q[T - 1][ps];
+        // second stored row: u^{k+T-1} of the row, or (difference form) d^{k+T}
+        const float(&pv)[4] = DF ? dtop : q[T - 1][ps];
         const int ro = rho - T * D;  // in [y0, y0 + L)
         if (w.interior) {
             const size_t o = off(g, w.xl, ro);
@@ -281,7 +386,7 @@ __device__ __forceinline__ void stream_group(const StreamWarp& w, const Geo& g, 
 // u^{k+T-1}.  Strip s covers output columns [x0, x0 + OW) with
 // x0 = (s % strips_x) OW and rows [y0, y0 + L) with y0 = (s / strips_x) L.
 // ring: this warp's NB input row slots (both planes) in shared memory.
-template <int S, bool PER, int T, bool WRAP>
+template <int S, bool PER, int T, bool WRAP, int M = kStreamPlain>
 __device__ __forceinline__ void stream_strip(const float* __restrict__ in_cur, const float* __restrict__ in_prev,
                                              float* __restrict__ out_cur, float* __restrict__ out_prev,
                                              const Geo& g, const Coef3<float>& a, int strips_x, int strip, int L,
@@ -313,24 +418,28 @@ __device__ __forceinline__ void stream_strip(const float* __restrict__ in_cur, c
     // q[t][slot][.]: level t (0 = u^k) at rows whose offset from rho0 is
     // congruent to slot modulo WIN
     float q[T][WIN][4];
+    float qd[T][WIN][4];  // difference form: d^t rows of levels 1 .. T-1
 #pragma unroll
     for (int t = 0; t < T; ++t)
 #pragma unroll
         for (int s = 0; s < WIN; ++s)
 #pragma unroll
-            for (int e = 0; e < 4; ++e) q[t][s][e] = 0.0f;
+            for (int e = 0; e < 4; ++e) q[t][s][e] = qd[t][s][e] = 0.0f;
 #pragma unroll
     for (int s = 0; s < PF; ++s) stream_issue<D, NB, WRAP>(w, g, s);
 
 #pragma unroll 1
     for (int base = 0; base < w.nsteps; base += WIN)
-        stream_group<S, PER, T, WRAP>(w, g, a, a10x2, a11x2, a20x2, q, base);
+        stream_group<S, PER, T, WRAP, M>(w, g, a, a10x2, a11x2, a20x2, q, qd, base);
     cp_async_wait_all();  // no copy may land in shared memory after the warp exits
 }
 
 // One grid: warp (blockIdx.x * kStreamWarps + warp) walks strip of that
-// index (strips_x strips across, n_strips in all).
-template <int S, bool PER, int T, bool WRAP>
+// index (strips_x strips across, n_strips in all).  M: kStreamPlain,
+// kStreamSums or kStreamForm (difference form: in_prev holds d^k and
+// out_prev receives d^{k+T}, rows read and written at the rows of u^k /
+// u^{k+T}).
+template <int S, bool PER, int T, bool WRAP, int M = kStreamPlain>
 __global__ void __launch_bounds__(kStreamWarps * 32)
     k5_stream(const float* __restrict__ in_cur, const float* __restrict__ in_prev, float* __restrict__ out_cur,
               float* __restrict__ out_prev, Geo g, Coef3<float> a, int strips_x, int n_strips, int L) {
@@ -339,8 +448,8 @@ __global__ void __launch_bounds__(kStreamWarps * 32)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int strip = blockIdx.x * kStreamWarps + warp;
     if (strip >= n_strips) return;  // whole warps only; no copies issued yet
-    stream_strip<S, PER, T, WRAP>(in_cur, in_prev, out_cur, out_prev, g, a, strips_x, strip, L,
-                                  stream_smem + warp * NB * 2 * 32, lane);
+    stream_strip<S, PER, T, WRAP, M>(in_cur, in_prev, out_cur, out_prev, g, a, strips_x, strip, L,
+                                      stream_smem + warp * NB * 2 * 32, lane);
 }
 
 // Periodic images of the two levels a streaming launch wrote, in the first gw

@@ -175,6 +175,17 @@ static bool is_multilevel(int kernel) { return kernel == WAVE2D_KERNEL_TEMPORAL 
 static bool multilevel_ok(const wave2d* h) {
     return h->nclass == 0 && h->bc != WAVE2D_BC_ODD && !((h->flags & WAVE2D_CANARY) && h->bc != WAVE2D_BC_ZERO);
 }
+// Handles the register-streaming kernel takes: FP32 storage; a Section 6
+// scheme, or a class chain of one to three classes (the 5-, 9- and 13-point
+// stencils: difference sums, difference form, or a derived scheme's plain
+// sums); boundary as multilevel_ok.  The difference form on a periodic grid
+// needs rows of whole vectors (the kernel reads d^k at wrapped coordinates;
+// no ring images of d^k are kept).
+static bool stream_ok(const wave2d* h) {
+    return h->dtype == DT_F32 && h->nclass <= 3 && h->bc != WAVE2D_BC_ODD &&
+           !((h->flags & WAVE2D_CANARY) && h->bc != WAVE2D_BC_ZERO) &&
+           (!h->diff_form || h->bc == WAVE2D_BC_ZERO || (h->nx % 4 == 0 && h->ny >= 16));
+}
 
 // ----------------------------------------------------------- TMA encoding
 static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
@@ -572,11 +583,12 @@ static int select_kernel(wave2d* h) {
         const int64_t nodes = (int64_t)h->nx * h->ny;
         const bool temporal_ok = multilevel_ok(h);
         want = (h->dtype != DT_F32 || nodes < 65536) ? WAVE2D_KERNEL_SIMPLE
-               : (temporal_ok && nodes >= (1 << 23)) ? WAVE2D_KERNEL_STREAM
+               : (stream_ok(h) && nodes >= (1 << 23)) ? WAVE2D_KERNEL_STREAM
                : (temporal_ok && nodes >= (1 << 20)) ? WAVE2D_KERNEL_TEMPORAL
-                                                     : WAVE2D_KERNEL_TMA;
+                                                      : WAVE2D_KERNEL_TMA;
     }
-    if (is_multilevel(want) && (h->dtype != DT_F32 || !multilevel_ok(h))) want = WAVE2D_KERNEL_TMA;
+    if (want == WAVE2D_KERNEL_TEMPORAL && (h->dtype != DT_F32 || !multilevel_ok(h))) want = WAVE2D_KERNEL_TMA;
+    if (want == WAVE2D_KERNEL_STREAM && !stream_ok(h)) want = WAVE2D_KERNEL_TMA;
     if (want == WAVE2D_KERNEL_PERSISTENT && (h->nclass > 0 || h->diff_sums || h->diff_form))
         want = WAVE2D_KERNEL_SIMPLE;
     if (want == WAVE2D_KERNEL_TMA && h->dtype == DT_F32X2) want = WAVE2D_KERNEL_SIMPLE;
@@ -590,8 +602,14 @@ static int select_kernel(wave2d* h) {
         // costs no extra columns; measured on GB300 at 4096^2: 9-point level
         // 13.4 us at T = 4, 11.7 at T = 6), 4 for the 13-point scheme (its
         // registers allow no deeper ring at 4 CTAs per SM)
+        // (difference form: 4 levels, 3 for the 13-point stencil, whose d
+        // rows take the registers of a deeper ring)
         const int tt = h->tune.temporal_t;
-        h->temporal_t = ((tt >= 2 && tt <= 4) || tt == 6) ? tt : (h->scheme == 13 ? 4 : 6);
+        const bool r2 = h->nclass == 0 ? h->scheme == 13 : h->nclass == 3;  // the 13-point stencil
+        if (h->diff_form)
+            h->temporal_t = (tt >= 2 && tt <= 4) ? tt : (r2 ? 3 : 4);
+        else
+            h->temporal_t = ((tt >= 2 && tt <= 4) || tt == 6) ? tt : (r2 ? 4 : 6);
         // rows per strip by default: 64 (measured on GB300 at 4096^2: the
         // 2RT rows a strip recomputes at its start cost less than the tail of
         // a second wave of strips; 64 rows make one wave of 2368 strips there)
@@ -627,13 +645,12 @@ constexpr int kGraphSteps = 48;
 
 // A graph of kGraphSteps levels (a multiple of 2 T for every depth the
 // multi-level kernels take) returns the levels to the planes they started
-// in, so one graph per starting (cur, prv) is replayed.
+// in, so one graph per starting (cur, prv, dpl) is replayed.
 static int run_graph(wave2d* h, int64_t& n) {
-    const int key = h->cur * 4 + h->prv;
+    const int key = h->plane_key();
     static_assert(kGraphSteps % 4 == 0 && kGraphSteps % 6 == 0 && kGraphSteps % 8 == 0 && kGraphSteps % 12 == 0,
                   "graph length must be a multiple of 2T");
     if (!h->graph[key]) {
-        const int cur0 = h->cur, prv0 = h->prv;
         const int64_t k0 = h->k;
         cudaGraph_t g = nullptr;
         W2D_CUDA(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
@@ -652,9 +669,8 @@ static int run_graph(wave2d* h, int64_t& n) {
         const int64_t launched = g_launches.load() - before;
         cudaError_t e = cudaStreamEndCapture(h->stream, &g);
         g_launches.store(before);  // captured launches run only when the graph does
-        h->graph_end[key] = h->cur * 4 + h->prv;
-        h->cur = cur0;
-        h->prv = prv0;
+        h->graph_end[key] = h->plane_key();
+        h->set_plane_key(key);
         h->k = k0;
         if (rc != WAVE2D_OK) {
             if (g) cudaGraphDestroy(g);
@@ -671,8 +687,7 @@ static int run_graph(wave2d* h, int64_t& n) {
         if (n >= kGraphSteps) {
             W2D_CUDA(cudaGraphLaunch(h->graph[key], h->stream), "graph launch");
             g_launches.fetch_add(h->graph_steps);
-            h->cur = h->graph_end[key] / 4;
-            h->prv = h->graph_end[key] % 4;
+            h->set_plane_key(h->graph_end[key]);
             h->k += kGraphSteps;
             n -= kGraphSteps;
         }
@@ -798,7 +813,10 @@ static int create_device_state(wave2d* h, const wave2d_grid* grid) {
     // (the temporal kernel writes out of place); FP32x2 keeps hi and lo
     // planes of two levels; FP64 two levels.
     h->elem = (h->dtype == WAVE2D_F64) ? 8 : 4;
-    h->nlevels = (h->dtype == WAVE2D_F32 && h->nclass == 0) ? 4 : h->diff_form ? 3 : 2;
+    // FP32: a second pair of planes for the out-of-place multi-level kernels
+    // (the Section 6 schemes and class chains of up to three classes); the
+    // difference form keeps u^k and d^k, each with a second plane
+    h->nlevels = (h->dtype == WAVE2D_F32 && (h->nclass <= 3 || h->diff_form)) ? 4 : 2;
     h->gw = h->R;
     h->G = kGhost;
     h->pitch = (int)round_up((size_t)h->nx + 2 * kGhost, 32);
@@ -955,9 +973,18 @@ int wave2d_set_tuning(wave2d_t h, const wave2d_tune* tune) {
                          "images fill the whole ghost ring)");
     if (multi && h->bc == WAVE2D_BC_ODD)
         return set_error(WAVE2D_ERR_ARG, "the temporal kernels cover the zero and periodic boundaries");
-    if (multi && h->nclass > 0)
+    if (tune->kernel == WAVE2D_KERNEL_TEMPORAL && h->nclass > 0)
         return set_error(WAVE2D_ERR_ARG,
-                         "the temporal kernels cover the 5-, 9- and 13-point schemes with plain sums only");
+                         "the tiled temporal kernel covers the 5-, 9- and 13-point schemes with plain sums only");
+    if (tune->kernel == WAVE2D_KERNEL_STREAM && h->nclass > 3)
+        return set_error(WAVE2D_ERR_ARG, "the streaming kernel covers stencils of at most three classes (13 points)");
+    if (tune->kernel == WAVE2D_KERNEL_STREAM && h->diff_form && !stream_ok(h))
+        return set_error(WAVE2D_ERR_ARG,
+                         "difference-form streaming takes the zero boundary or a periodic grid with nx %% 4 == 0, "
+                         "ny >= 16");
+    if (tune->kernel == WAVE2D_KERNEL_STREAM && h->diff_form && tune->temporal_t > 4)
+        return set_error(WAVE2D_ERR_ARG, "temporal_t of difference-form streaming must be 0 (auto), 2, 3 or 4 (got %d)",
+                         tune->temporal_t);
     if (tune->kernel == WAVE2D_KERNEL_TEMPORAL &&
         !(tune->temporal_t == 0 || (tune->temporal_t >= 2 && tune->temporal_t <= 4)))
         return set_error(WAVE2D_ERR_ARG, "temporal_t of the tiled kernel must be 0 (auto), 2, 3 or 4 (got %d)",
@@ -1045,6 +1072,7 @@ int wave2d_first_step(wave2d_t h, const double* u0, const double* v0, int on_dev
         dv0 = (const double*)stage + n;
     }
     W2D_CUDA(cudaMemsetAsync(h->acc_track, 0, 4 * sizeof(double), h->stream), "reset accumulators");
+    h->dpl = 2;  // difference form: d^1 goes to plane 2
     int rc = launch_first_step(h, du0, dv0);
     if (stage) dev_free(h->alloc, stage, 2 * n * sizeof(double), h->stream);
     if (rc != WAVE2D_OK) return rc;
@@ -1146,7 +1174,7 @@ int wave2d_get_state(wave2d_t h, double* u_prev, double* u_cur, int64_t* k) {
     if (!stage) return set_error(WAVE2D_ERR_OOM, "staging allocation failed");
     dispatch_dt(h->dtype, [&](auto DTc) {
         constexpr int DT = decltype(DTc)::value;
-        k_pack<DT><<<grid2d(h), dim3(32, 8), 0, h->stream>>>(h->level(h->diff_form ? 2 : h->prv), h->geo(), stage);
+        k_pack<DT><<<grid2d(h), dim3(32, 8), 0, h->stream>>>(h->level(h->diff_form ? h->dpl : h->prv), h->geo(), stage);
         k_pack<DT><<<grid2d(h), dim3(32, 8), 0, h->stream>>>(h->level(h->cur), h->geo(), stage + n);
         if (h->diff_form)  // u^{k-1} = u^k - d^k, in FP64
             k_combine<<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(stage + n, stage, stage, n);
@@ -1182,6 +1210,7 @@ int wave2d_set_state(wave2d_t h, const double* u_prev, const double* u_cur, int6
     }
     h->cur = 0;
     h->prv = 1;
+    h->dpl = 2;
     double* dstage = nullptr;
     if (h->diff_form) {  // d^k = u^k - u^{k-1}, formed in FP64
         dstage = (double*)dev_alloc(h->alloc, n * sizeof(double), h->stream);
@@ -1196,7 +1225,7 @@ int wave2d_set_state(wave2d_t h, const double* u_prev, const double* u_cur, int6
         constexpr int DT = decltype(DTc)::value;
         dispatch_bc(h->bc, [&](auto Pc) {
             k_unpack<DT, decltype(Pc)::value><<<grid2d(h), dim3(32, 8), 0, h->stream>>>(
-                dp, h->level(h->diff_form ? 2 : 1), h->geo(), h->gw);
+                dp, h->level(h->diff_form ? h->dpl : 1), h->geo(), h->gw);
             k_unpack<DT, decltype(Pc)::value><<<grid2d(h), dim3(32, 8), 0, h->stream>>>(dc, h->level(0), h->geo(), h->gw);
         });
     });
@@ -1223,7 +1252,7 @@ int wave2d_get_raw(wave2d_t h, void* dst, int64_t bytes, int64_t* k) {
     if (!h->initialized) return set_error(WAVE2D_ERR_STATE, "no state yet");
     if (bytes < wave2d_raw_bytes(h)) return set_error(WAVE2D_ERR_ARG, "buffer too small");
     char* d = (char*)dst;
-    const int order[2] = {h->diff_form ? 2 : h->prv, h->cur};
+    const int order[2] = {h->diff_form ? h->dpl : h->prv, h->cur};
     for (int q = 0; q < 2; ++q) {
         W2D_CUDA(cudaMemcpyAsync(d + q * h->plane_bytes, h->hi[order[q]], h->plane_bytes, cudaMemcpyDeviceToHost,
                                  h->stream),
@@ -1245,8 +1274,9 @@ int wave2d_set_raw(wave2d_t h, const void* src, int64_t bytes, int64_t k) {
     const char* s = (const char*)src;
     h->cur = 1;  // plane 0 <- u^{k-1}, plane 1 <- u^k (difference form: plane 2 <- d^k)
     h->prv = 0;
+    h->dpl = 2;
     for (int q = 0; q < 2; ++q) {
-        const int plane = (q == 0 && h->diff_form) ? 2 : q;
+        const int plane = (q == 0 && h->diff_form) ? h->dpl : q;
         W2D_CUDA(cudaMemcpyAsync(h->hi[plane], s + q * h->plane_bytes, h->plane_bytes, cudaMemcpyHostToDevice,
                                  h->stream),
                  "raw copy");
@@ -1278,7 +1308,7 @@ static int copy_rows(wave2d* h, int j0, int nrows, void* prev, void* cur, const 
     const size_t el = h->elem, rowb = (size_t)h->nx * el, block = rowb * nrows;
     const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice
                                           : (to_handle ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToHost);
-    const int planes[2] = {h->diff_form ? 2 : h->prv, h->cur};
+    const int planes[2] = {h->diff_form ? h->dpl : h->prv, h->cur};
     for (int q = 0; q < 2; ++q) {
         char* ext = static_cast<char*>(to_handle ? const_cast<void*>(q ? ccur : cprev) : (q ? cur : prev));
         if (!ext) return set_error(WAVE2D_ERR_ARG, "null row buffer");
@@ -1436,6 +1466,10 @@ int wave2d_autotune(wave2d_t h, int64_t steps, wave2d_tune* best) {
         add(WAVE2D_KERNEL_TMA, 0, 0, 1);
         add(WAVE2D_KERNEL_TMA, 0, 0, 2);
         add(WAVE2D_KERNEL_SIMPLE, 0, 0, 0);
+        if (stream_ok(h))
+            for (int T : {2, 3, 4, 6})
+                for (int rows : {16, 32, 64})
+                    if (T <= 4 || !h->diff_form) add(WAVE2D_KERNEL_STREAM, rows, T, 0);
     } else if (h->dtype == WAVE2D_F32) {
         add(WAVE2D_KERNEL_TMA, 0, 0, 1);
         add(WAVE2D_KERNEL_TMA, 0, 0, 2);
@@ -1462,10 +1496,10 @@ int wave2d_autotune(wave2d_t h, int64_t steps, wave2d_tune* best) {
     const size_t snap_bytes = 2 * (size_t)np * h->plane_bytes;
     char* snap = (char*)dev_alloc(h->alloc, snap_bytes, h->stream);
     if (!snap) return set_error(WAVE2D_ERR_OOM, "autotune snapshot allocation failed");
-    const int cur0 = h->cur, prv0 = h->prv;
+    const int cur0 = h->cur, prv0 = h->prv, dpl0 = h->dpl;
     const int64_t k0 = h->k;
     auto copy_levels = [&](bool save) -> int {
-        const int planes[2] = {cur0, h->diff_form ? 2 : prv0};
+        const int planes[2] = {cur0, h->diff_form ? dpl0 : prv0};
         for (int q = 0; q < 2; ++q)
             for (int part = 0; part < np; ++part) {
                 void* dev = part == 0 ? h->hi[planes[q]] : h->lo[planes[q]];
@@ -1476,6 +1510,7 @@ int wave2d_autotune(wave2d_t h, int64_t steps, wave2d_tune* best) {
             }
         h->cur = cur0;
         h->prv = prv0;
+        h->dpl = dpl0;
         h->k = k0;
         return WAVE2D_OK;
     };

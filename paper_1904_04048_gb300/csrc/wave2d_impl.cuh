@@ -67,7 +67,8 @@ struct wave2d {
     int nclass = 0, npoints = 0;
     double ca[8] = {}, cb[8] = {};
     bool diff_sums = false;  // WAVE2D_DIFF_SUMS: class sums from differences to the centre
-    bool diff_form = false;  // WAVE2D_DIFF_FORM: planes u^k (cur), scratch (prv), d^k (plane 2)
+    bool diff_form = false;  // WAVE2D_DIFF_FORM: planes u^k (cur), scratch (prv), d^k (dpl)
+    int dpl = 2;             // difference form: plane of d^k (2 or 3; the streaming kernel alternates them)
     // device
     int device = 0, num_sms = 0, l2_bytes = 0;
     cudaStream_t stream = nullptr;
@@ -108,8 +109,15 @@ struct wave2d {
     bool tma_ready = false;
     int reg_key = -1;
     // captured runs of steps, keyed by the starting (cur, prv) planes
-    cudaGraphExec_t graph[16] = {};
-    int graph_end[16] = {};  // (cur, prv) after a replay, as cur * 4 + prv
+    cudaGraphExec_t graph[32] = {};
+    int graph_end[32] = {};  // plane state after a replay, as plane_key()
+    // (cur, prv, dpl) as one index: the key of a captured graph
+    int plane_key() const { return (dpl & 1) * 16 + cur * 4 + prv; }
+    void set_plane_key(int key) {
+        dpl = 2 + key / 16;
+        cur = key % 16 / 4;
+        prv = key % 4;
+    }
     int graph_steps = 0;
 
     w2d::Level level(int p) const { return w2d::Level{hi[p], lo[p]}; }
