@@ -146,9 +146,10 @@ typedef struct wave2d *wave2d_t;
 
 /* Kernel selection for the two-step.  Zero-initialised = automatic: the
  * one-node kernel below 65536 nodes and for FP64 / FP32x2, the TMA kernel for
- * FP32, and for the FP32 Section 6 schemes on the zero and periodic
- * boundaries (with WAVE2D_CANARY the zero boundary only) the temporal kernel
- * (T = 4) from 2^20 nodes and the streaming kernel (T = 4) from 2^23 nodes. */
+ * FP32, and where the streaming kernel applies (below) that kernel from 2^20
+ * nodes (the Section 6 schemes with plain sums) or 2^18 nodes (class chains
+ * of one to three classes: difference sums, the difference form, derived
+ * schemes). */
 enum {
     WAVE2D_KERNEL_AUTO = 0,
     WAVE2D_KERNEL_SIMPLE = 1,   /* one thread per node, global loads            */
@@ -165,23 +166,29 @@ enum {
                                    level; the Section 6 schemes with plain sums,
                                    any storage type and boundary               */
 };
-/* The two multi-level kernels (TEMPORAL, STREAM) take FP32 handles of the
- * 5-, 9- and 13-point schemes on the zero and periodic boundaries (with
- * WAVE2D_CANARY the zero boundary only); they write out of place (the handle's second pair of level
- * planes) and finish a run whose length is not a multiple of T with TMA
- * single steps.  Every kernel evaluates each node identically, so the choice
- * changes no result bit. */
+/* The two multi-level kernels (TEMPORAL, STREAM) take FP32 handles on the
+ * zero and periodic boundaries (with WAVE2D_CANARY the zero boundary only):
+ * TEMPORAL the 5-, 9- and 13-point schemes with plain sums; STREAM those and
+ * every class chain of one to three classes (WAVE2D_DIFF_SUMS,
+ * WAVE2D_DIFF_FORM, derived schemes of up to 13 points), the difference form
+ * on a periodic grid only with nx a multiple of 4 and ny >= 16.  They write
+ * out of place (the handle's second pair of level planes; the difference
+ * form alternates u^k and d^k between two planes each) and finish a run
+ * whose length is not a multiple of T with TMA single steps.  Every kernel
+ * evaluates each node identically, so the choice changes no result bit. */
 
 typedef struct {
     int32_t kernel;       /* WAVE2D_KERNEL_*                                      */
     int32_t tile_h;       /* output rows per tile of WAVE2D_KERNEL_TEMPORAL: 16,
                              24, 32 or 64 (0 = 24 for 9 points, else 32); output
                              rows per strip of WAVE2D_KERNEL_STREAM: 8 .. 4096
-                             (0 = 64)                                             */
+                             (0 = the most of 64, 32 and 16 that makes at
+                             least 6 strips per SM)                               */
     int32_t temporal_t;   /* steps per launch of the multi-level kernels: 2, 3 or
                              4 for WAVE2D_KERNEL_TEMPORAL (0 = 4); 2, 3, 4 or 6
                              for WAVE2D_KERNEL_STREAM (0 = 4 for 13 points, 6
-                             for 5 and 9 points)                                  */
+                             for 5 and 9 points), 2, 3 or 4 in the difference
+                             form (0 = 3 for 13 points, else 4)                   */
     int32_t use_graph;    /* capture runs of steps in a CUDA graph: 1 on, 0 off,
                              -1 automatic                                         */
     int32_t ctas_per_sm;  /* resident CTAs per SM for the TMA kernels; 0 = auto:

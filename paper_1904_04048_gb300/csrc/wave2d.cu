@@ -573,19 +573,23 @@ static void drop_graphs(wave2d* h) {
 static int select_kernel(wave2d* h) {
     int want = h->tune.kernel;
     if (want == WAVE2D_KERNEL_AUTO) {
-        // FP32: TMA tiles once the grid fills the GPU; where the multi-level
-        // kernels apply, the shared-memory temporal kernel from 2^20 nodes and
-        // the register-streaming kernel from 2^23 (measured on GB300: at
-        // 2048^2 the two tie or the temporal kernel leads, from 4096^2 on the
-        // streaming kernel is faster for every Section 6 scheme).  FP64 and
-        // FP32x2 are bound by arithmetic on GB300 (measured: the one-node
-        // kernel is as fast at 4096^2 and 2.4x faster at 256^2), so they keep it.
+        // FP32: TMA tiles once the grid fills the GPU; where the streaming
+        // kernel applies, that kernel from 2^20 nodes (the Section 6 schemes;
+        // measured on GB300 with its default strip rows against the tiled
+        // temporal kernel: 1.1-1.7x faster at 1024^2, 1.4-2.2x at 2048^2,
+        // 1.3-2.3x at 4096^2) or 2^18 (class chains of up to three classes,
+        // which have no tiled temporal kernel: against their one-level TMA
+        // kernel, 9- and 13-point, sums and form, 1.1-1.9x at 512^2 and
+        // 1024^2, 1.5-2.1x at 2048^2, 1.6-3.1x at 4096^2).  The tiled
+        // temporal kernel stays available by name and to the autotuner.
+        // FP64 and FP32x2 are bound by arithmetic on GB300 (measured: the
+        // one-node kernel is as fast at 4096^2 and 2.4x faster at 256^2), so
+        // they keep it.
         const int64_t nodes = (int64_t)h->nx * h->ny;
-        const bool temporal_ok = multilevel_ok(h);
-        want = (h->dtype != DT_F32 || nodes < 65536) ? WAVE2D_KERNEL_SIMPLE
-               : (stream_ok(h) && nodes >= (1 << 23)) ? WAVE2D_KERNEL_STREAM
-               : (temporal_ok && nodes >= (1 << 20)) ? WAVE2D_KERNEL_TEMPORAL
-                                                      : WAVE2D_KERNEL_TMA;
+        const int64_t stream_from = h->nclass > 0 ? (1 << 18) : (1 << 20);
+        want = (h->dtype != DT_F32 || nodes < 65536)    ? WAVE2D_KERNEL_SIMPLE
+               : (stream_ok(h) && nodes >= stream_from) ? WAVE2D_KERNEL_STREAM
+                                                        : WAVE2D_KERNEL_TMA;
     }
     if (want == WAVE2D_KERNEL_TEMPORAL && (h->dtype != DT_F32 || !multilevel_ok(h))) want = WAVE2D_KERNEL_TMA;
     if (want == WAVE2D_KERNEL_STREAM && !stream_ok(h)) want = WAVE2D_KERNEL_TMA;
@@ -610,10 +614,20 @@ static int select_kernel(wave2d* h) {
             h->temporal_t = (tt >= 2 && tt <= 4) ? tt : (r2 ? 3 : 4);
         else
             h->temporal_t = ((tt >= 2 && tt <= 4) || tt == 6) ? tt : (r2 ? 4 : 6);
-        // rows per strip by default: 64 (measured on GB300 at 4096^2: the
-        // 2RT rows a strip recomputes at its start cost less than the tail of
-        // a second wave of strips; 64 rows make one wave of 2368 strips there)
-        h->temporal_oh = h->tune.tile_h > 0 ? h->tune.tile_h : 64;
+        // rows per strip by default: the most of 64, 32 and 16 that still
+        // makes at least 6 strips per SM (measured on GB300: the 2RT rows a
+        // strip recomputes at its start cost less than a second wave of
+        // strips, but a grid of too few strips leaves SMs idle; 4096^2 takes
+        // 64 rows, 2368 strips; 2048^2 32 rows; 1024^2 and below 16)
+        if (h->tune.tile_h > 0) {
+            h->temporal_oh = h->tune.tile_h;
+        } else {
+            const int hx = (h->R * h->temporal_t + 3) / 4 * 4, ow = 128 - 2 * hx;
+            const int64_t sx = (h->nx + ow - 1) / ow, want_strips = 6 * (int64_t)h->num_sms;
+            h->temporal_oh = sx * ((h->ny + 63) / 64) >= want_strips   ? 64
+                             : sx * ((h->ny + 31) / 32) >= want_strips ? 32
+                                                                       : 16;
+        }
     }
     if (want == WAVE2D_KERNEL_TEMPORAL) {
         const int tt = h->tune.temporal_t;

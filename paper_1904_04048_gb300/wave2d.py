@@ -441,7 +441,7 @@ class Wave2D:
         TEMPORAL / STREAM; ``tile_h`` rows per tile (TEMPORAL: 16, 24, 32, 64)
         or per strip (STREAM: 8 .. 4096), 0 = default; ``temporal_t`` levels
         per launch of the two multi-level kernels (TEMPORAL: 2, 3, 4; STREAM:
-        2, 3, 4, 6; 0 = the default depth)."""
+        2, 3, 4, 6, in the difference form 2, 3, 4; 0 = the default depth)."""
         t = wave2d_tune(int(kernel), int(tile_h), int(temporal_t), int(use_graph), int(ctas_per_sm))
         check(lib().wave2d_set_tuning(self._h, ctypes.byref(t)))
 
