@@ -145,11 +145,9 @@ typedef struct {
 typedef struct wave2d *wave2d_t;
 
 /* Kernel selection for the two-step.  Zero-initialised = automatic: the
- * one-node kernel below 65536 nodes and for FP64 / FP32x2, the TMA kernel for
- * FP32, and where the streaming kernel applies (below) that kernel from 2^20
- * nodes (the Section 6 schemes with plain sums) or 2^18 nodes (class chains
- * of one to three classes: difference sums, the difference form, derived
- * schemes). */
+ * one-node kernel below 65536 nodes and for FP64 / FP32x2; from 65536 nodes
+ * in FP32 the streaming kernel where it applies (below: the Section 6 schemes
+ * and class chains of one to three classes), else the TMA kernel. */
 enum {
     WAVE2D_KERNEL_AUTO = 0,
     WAVE2D_KERNEL_SIMPLE = 1,   /* one thread per node, global loads            */

@@ -472,7 +472,6 @@ __device__ __forceinline__ bool grid_barrier(unsigned long long* arrived, unsign
                 ok = 0;
                 break;
             }
-            __nanosleep(32);
         }
         __threadfence();  // the other blocks' stores before this block's next reads
     }
@@ -481,7 +480,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned long long* arrived, unsign
 }
 
 template <int DT, int S, int BCM>
-__global__ void __launch_bounds__(256) k2_persist(Level A, Level B, Geo g, Coef3<typename St<DT>::V> a,
+__global__ void __launch_bounds__(512) k2_persist(Level A, Level B, Geo g, Coef3<typename St<DT>::V> a,
                                                   int n_levels, unsigned long long* arrived, int* status, int gw,
                                                   long long limit) {
     using T = St<DT>;

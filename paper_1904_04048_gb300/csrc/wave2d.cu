@@ -480,14 +480,22 @@ static int launch_temporal(wave2d* h) {
 template <int DT, int S, int BCM>
 static int launch_persist_t(wave2d* h, int n) {
     auto kern = k2_persist<DT, S, BCM>;
-    static int per_sm = -1;  // resident blocks of 256 threads per SM for this instantiation
+    static int per_sm = -1;  // resident blocks of 512 threads per SM for this instantiation
     if (per_sm < 0) {
         int v = 0;
-        W2D_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, kern, 256, 0), "occupancy query");
+        W2D_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, kern, 512, 0), "occupancy query");
         per_sm = std::max(1, v);
     }
+    // One block per SM with the nodes spread evenly (blocks of 64 .. 512
+    // threads), more blocks of 512 only where a block per SM cannot hold a
+    // node per thread: every SM then carries the same share of a level (at
+    // 256^2 FP64 the level's arithmetic, not memory, sets its length, and
+    // 256 blocks on 152 SMs gave two thirds of the SMs twice the work).
     const long long nn = (long long)h->nx * h->ny;
-    const int blocks = (int)std::max<long long>(1, std::min<long long>((nn + 255) / 256, (long long)per_sm * h->num_sms));
+    const long long per_block = (nn + h->num_sms - 1) / h->num_sms;
+    const int threads = (int)std::min<long long>(512, std::max<long long>(64, (per_block + 31) / 32 * 32));
+    const int blocks = (int)std::max<long long>(
+        1, std::min<long long>((nn + threads - 1) / threads, (long long)per_sm * h->num_sms));
     unsigned long long* arrived = reinterpret_cast<unsigned long long*>(reinterpret_cast<char*>(h->counter) + 128);
     W2D_CUDA(cudaMemsetAsync(arrived, 0, sizeof(unsigned long long), h->stream), "barrier reset");
     Level A = h->level(h->cur), B = h->level(h->prv);
@@ -497,7 +505,7 @@ static int launch_persist_t(wave2d* h, int n) {
     int gw = h->gw;
     long long limit = kWaitLimitCycles;
     void* args[] = {&A, &B, &g, &a, &n, &arrived, &status, &gw, &limit};
-    W2D_CUDA(cudaLaunchCooperativeKernel((const void*)kern, dim3(blocks), dim3(256), args, 0, h->stream),
+    W2D_CUDA(cudaLaunchCooperativeKernel((const void*)kern, dim3(blocks), dim3(threads), args, 0, h->stream),
              "persistent kernel launch");
     W2D_LAUNCHED("persistent kernel launch");
     return WAVE2D_OK;
@@ -573,23 +581,22 @@ static void drop_graphs(wave2d* h) {
 static int select_kernel(wave2d* h) {
     int want = h->tune.kernel;
     if (want == WAVE2D_KERNEL_AUTO) {
-        // FP32: TMA tiles once the grid fills the GPU; where the streaming
-        // kernel applies, that kernel from 2^20 nodes (the Section 6 schemes;
-        // measured on GB300 with its default strip rows against the tiled
-        // temporal kernel: 1.1-1.7x faster at 1024^2, 1.4-2.2x at 2048^2,
-        // 1.3-2.3x at 4096^2) or 2^18 (class chains of up to three classes,
-        // which have no tiled temporal kernel: against their one-level TMA
-        // kernel, 9- and 13-point, sums and form, 1.1-1.9x at 512^2 and
-        // 1024^2, 1.5-2.1x at 2048^2, 1.6-3.1x at 4096^2).  The tiled
-        // temporal kernel stays available by name and to the autotuner.
-        // FP64 and FP32x2 are bound by arithmetic on GB300 (measured: the
-        // one-node kernel is as fast at 4096^2 and 2.4x faster at 256^2), so
-        // they keep it.
+        // FP32: the streaming kernel wherever it applies, the TMA kernel for
+        // other handles, from 65536 nodes.  Measured on GB300 (periodic,
+        // streaming with its default depth and strip rows): the Section 6
+        // schemes 1.4-2.0x faster than the TMA kernel and 1.1-1.5x faster than
+        // the tiled temporal kernel at 256^2 - 768^2, 1.1-1.7x (temporal) at
+        // 1024^2, 1.4-2.2x at 2048^2, 1.3-2.3x at 4096^2; the class chains of
+        // up to three classes (which have no tiled temporal kernel) 1.1-1.9x
+        // faster than their one-level TMA kernel at 512^2 and 1024^2, 1.5-2.1x
+        // at 2048^2, 1.6-3.1x at 4096^2.  The tiled temporal kernel stays
+        // available by name and to the autotuner.  FP64 and FP32x2 are bound
+        // by arithmetic on GB300 (measured: the one-node kernel is as fast at
+        // 4096^2 and 2.4x faster at 256^2), so they keep it.
         const int64_t nodes = (int64_t)h->nx * h->ny;
-        const int64_t stream_from = h->nclass > 0 ? (1 << 18) : (1 << 20);
-        want = (h->dtype != DT_F32 || nodes < 65536)    ? WAVE2D_KERNEL_SIMPLE
-               : (stream_ok(h) && nodes >= stream_from) ? WAVE2D_KERNEL_STREAM
-                                                        : WAVE2D_KERNEL_TMA;
+        want = (h->dtype != DT_F32 || nodes < 65536) ? WAVE2D_KERNEL_SIMPLE
+               : stream_ok(h)                        ? WAVE2D_KERNEL_STREAM
+                                                     : WAVE2D_KERNEL_TMA;
     }
     if (want == WAVE2D_KERNEL_TEMPORAL && (h->dtype != DT_F32 || !multilevel_ok(h))) want = WAVE2D_KERNEL_TMA;
     if (want == WAVE2D_KERNEL_STREAM && !stream_ok(h)) want = WAVE2D_KERNEL_TMA;
