@@ -23,7 +23,8 @@ NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", 
               "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off", "-I" + os.path.join(ROOT, "include")]
 
 SOURCES = ["wave2d.cu", "chain.cu", "chain_f32.cu", "chain_f64.cu", "chain_f32x2.cu", "chain_tma.cu", "scheme.cu",
-           "noalloc.cu", "batch.cu", "server.cu", "canary.cu", "stream.cu", "peaks.cu"]
+           "noalloc.cu", "batch.cu", "server.cu", "canary.cu", "stream.cu", "peaks.cu",
+           "df2.cu"]
 
 
 def _nvcc():

@@ -1,0 +1,189 @@
+// Two-step (Eq. A2) on double-float storage ("FP32x2", hi + lo planes), two
+// neighbouring nodes per thread in packed f32x2 arithmetic.
+//
+// The double-float level is bound by FP32 arithmetic (about 200 operations
+// per 13-point node-update: the error-free sums of stencil_ops.cuh), and the
+// one-node kernel spends as many issue slots again on loads, addresses and
+// moves: measured on GB300 at 4096^2, issue 78 % active with 3.8 eligible
+// warps per scheduler, 167 us per level.  Here a thread updates nodes i and
+// i + 1 of a row: every double-float operation whose operands are register
+// pairs (the centre, the north/south and second-ring neighbours, the
+// coefficient products, 2u^k - u^{k-1}, the final sum) runs as packed
+// add/sub/mul/fma .rn.f32x2, one instruction for both nodes, and the rows
+// arrive as 8-byte loads.  Sums whose operands straddle a register pair (east
+// + west and the diagonals) run as scalar double-float sums per node, whose
+// results then form a pair.
+//
+// Bitwise equality with the one-node kernel: each lane performs the
+// operations of lambda_sum / two_step_update on df (stencil_ops.cuh) in the
+// same order with the same roundings.  Subtractions of a negated operand use
+// the identities a + (-b) = a - b and -(x) rounded = -(x rounded), both exact
+// in IEEE arithmetic, so a packed subtraction replaces an addition of a
+// negated value without changing a bit.  Explicit .rn operations are not
+// contracted into fused operations.
+#include "kernels.cuh"
+#include "wave2d_impl.cuh"
+
+namespace w2d {
+
+namespace {
+
+__device__ __forceinline__ f2x sub2(f2x a, f2x b) {
+    f2x d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+struct df2 {
+    f2x hi, lo;  // lane 0: node i, lane 1: node i + 1
+};
+
+__device__ __forceinline__ f2x dup2(float v) { return pk2(v, v); }
+
+// TwoSum, Fast2Sum and Dekker's double-length sum lane by lane (df_add).
+__device__ __forceinline__ df2 df2_add(const df2& x, const df2& y) {
+    const f2x s = add2(x.hi, y.hi);
+    const f2x bb = sub2(s, x.hi);
+    const f2x t = add2(sub2(x.hi, sub2(s, bb)), sub2(y.hi, bb));
+    const f2x e = add2(add2(t, x.lo), y.lo);
+    const f2x h = add2(s, e);
+    return {h, sub2(e, sub2(h, s))};
+}
+// df_add(x, df_neg(y)): x.hi + (-y.hi) = x.hi - y.hi; (-y.hi) - bb =
+// -(y.hi + bb), added as a subtraction; the low parts likewise.
+__device__ __forceinline__ df2 df2_sub(const df2& x, const df2& y) {
+    const f2x s = sub2(x.hi, y.hi);
+    const f2x bb = sub2(s, x.hi);
+    const f2x t = sub2(sub2(x.hi, sub2(s, bb)), add2(y.hi, bb));
+    const f2x e = sub2(add2(t, x.lo), y.lo);
+    const f2x h = add2(s, e);
+    return {h, sub2(e, sub2(h, s))};
+}
+// df_mul(a, x) with a a coefficient (the same for both lanes).  The product
+// p = a.hi x.hi is carried negated, pn = (-a.hi) x.hi = -p exactly, so that
+// fma(a.hi, x.hi, -p) takes pn as its addend; the closing Fast2Sum of p and
+// the error e is then s = e - pn (= p + e), err = e - (s + pn) (= e - (s - p)).
+__device__ __forceinline__ df2 df2_mul(f2x ahi, f2x nahi, f2x alo, const df2& x) {
+    const f2x pn = mul2(nahi, x.hi);
+    f2x e = fma2(ahi, x.hi, pn);
+    e = fma2(ahi, x.lo, e);
+    e = fma2(alo, x.hi, e);
+    const f2x s = sub2(e, pn);
+    return {s, sub2(e, add2(s, pn))};
+}
+__device__ __forceinline__ df2 df2_scale(const df2& x, float s) { return {mul2(x.hi, dup2(s)), mul2(x.lo, dup2(s))}; }
+
+__device__ __forceinline__ f2x ld2(const float* p, size_t o) {
+    return __ldg(reinterpret_cast<const unsigned long long*>(p + o));
+}
+// Row segment of a level: the hi and lo pairs at columns (x, x + 1) for x = i - 2, i, i + 2.
+struct Row6 {
+    df2 m, c, p;
+};
+__device__ __forceinline__ df2 ldp(const Level& L, size_t o) {
+    return {ld2((const float*)L.hi, o), ld2((const float*)L.lo, o)};
+}
+__device__ __forceinline__ Row6 ld_row6(const Level& L, size_t o) { return {ldp(L, o - 2), ldp(L, o), ldp(L, o + 2)}; }
+
+__device__ __forceinline__ df lane(const df2& v, int k) {
+    float h0, h1, l0, l1;
+    upk2(v.hi, h0, h1);
+    upk2(v.lo, l0, l1);
+    return k == 0 ? df{h0, l0} : df{h1, l1};
+}
+__device__ __forceinline__ df2 pack(const df& a, const df& b) { return {pk2(a.hi, b.hi), pk2(a.lo, b.lo)}; }
+
+// The value at column offset d in -2 .. 3 from the pair's first node.
+__device__ __forceinline__ df at(const Row6& r, int d) {
+    return d < 0 ? lane(r.m, d + 2) : d < 2 ? lane(r.c, d) : lane(r.p, d - 2);
+}
+
+}  // namespace
+
+template <int S, int BCM>
+__global__ void __launch_bounds__(256) k2_df2(Level cur, Level nxt, Geo g, Coef3<df> a, int gw) {
+    const int i0 = 2 * (blockIdx.x * 32 + threadIdx.x);
+    const int j = blockIdx.y * 8 + threadIdx.y;
+    if (i0 >= g.nx || j >= g.ny) return;
+    const bool two = i0 + 1 < g.nx;  // an odd row width leaves the last pair one node
+    const size_t o = off(g, i0, j);   // i0 + G even: 8-byte aligned pairs
+    const size_t P = (size_t)g.pitch;
+
+    const Row6 C = ld_row6(cur, o);
+    const df2 c = C.c;
+    const df2 m4c = df2_scale(c, -4.0f);
+    // class (1,0): (e + w) + (n + s), then -4 u_ij
+    const df2 ew = pack(df_add(at(C, 1), at(C, -1)), df_add(at(C, 2), at(C, 0)));
+    df2 nrow, srow;
+    Row6 N, Sr;
+    if constexpr (S >= 9) {
+        N = ld_row6(cur, o + P);
+        Sr = ld_row6(cur, o - P);
+        nrow = N.c;
+        srow = Sr.c;
+    } else {
+        nrow = ldp(cur, o + P);
+        srow = ldp(cur, o - P);
+    }
+    const df2 d10 = df2_add(df2_add(ew, df2_add(nrow, srow)), m4c);
+    df2 L = df2_mul(dup2(a.a10.hi), dup2(-a.a10.hi), dup2(a.a10.lo), d10);
+    if constexpr (S >= 9) {
+        // class (1,1): (ne + sw) + (nw + se)
+        const df2 nesw = pack(df_add(at(N, 1), at(Sr, -1)), df_add(at(N, 2), at(Sr, 0)));
+        const df2 nwse = pack(df_add(at(N, -1), at(Sr, 1)), df_add(at(N, 0), at(Sr, 2)));
+        const df2 d11 = df2_add(df2_add(nesw, nwse), m4c);
+        L = df2_add(df2_mul(dup2(a.a11.hi), dup2(-a.a11.hi), dup2(a.a11.lo), d11), L);
+    }
+    if constexpr (S == 13) {
+        // class (2,0): (ee + ww) + (nn + ss)
+        const df2 nn = ldp(cur, o + 2 * P), ss = ldp(cur, o - 2 * P);
+        const df2 d20 = df2_add(df2_add(df2_add(C.p, C.m), df2_add(nn, ss)), m4c);
+        L = df2_add(df2_mul(dup2(a.a20.hi), dup2(-a.a20.hi), dup2(a.a20.lo), d20), L);
+    }
+    // u^{k-1} from the plane this thread overwrites with u^{k+1}: plain loads
+    const df2 prev = {*reinterpret_cast<const unsigned long long*>((const float*)nxt.hi + o),
+                      *reinterpret_cast<const unsigned long long*>((const float*)nxt.lo + o)};
+    const df2 r = df2_add(df2_sub(df2_scale(c, 2.0f), prev), L);
+
+    const df r0 = lane(r, 0), r1 = lane(r, 1);
+    if (two) {
+        *reinterpret_cast<unsigned long long*>((float*)nxt.hi + o) = r.hi;
+        *reinterpret_cast<unsigned long long*>((float*)nxt.lo + o) = r.lo;
+    } else {
+        ((float*)nxt.hi)[o] = r0.hi;
+        ((float*)nxt.lo)[o] = r0.lo;
+    }
+    if constexpr (BCM != BCM_ZERO) {
+        write_images_bc<DT_F32X2, BCM>(nxt, g, i0, j, r0, gw);
+        if (two) write_images_bc<DT_F32X2, BCM>(nxt, g, i0 + 1, j, r1, gw);
+    }
+}
+
+template <int S>
+static void launch_df2_s(wave2d* h, const Coef3<df>& a, dim3 grid) {
+    const Level cur = h->level(h->cur), nxt = h->level(h->prv);
+    switch (h->bc) {
+        case WAVE2D_BC_PERIODIC:
+            k2_df2<S, BCM_PERIODIC><<<grid, dim3(32, 8), 0, h->stream>>>(cur, nxt, h->geo(), a, h->gw);
+            break;
+        case WAVE2D_BC_ODD:
+            k2_df2<S, BCM_ODD><<<grid, dim3(32, 8), 0, h->stream>>>(cur, nxt, h->geo(), a, h->gw);
+            break;
+        default:
+            k2_df2<S, BCM_ZERO><<<grid, dim3(32, 8), 0, h->stream>>>(cur, nxt, h->geo(), a, h->gw);
+            break;
+    }
+}
+
+int df2_simple_step(wave2d* h, const Coef3<df>& a) {
+    const dim3 grid((((h->nx + 1) / 2) + 31) / 32, (h->ny + 7) / 8);
+    switch (h->scheme) {
+        case 5: launch_df2_s<5>(h, a, grid); break;
+        case 9: launch_df2_s<9>(h, a, grid); break;
+        default: launch_df2_s<13>(h, a, grid); break;
+    }
+    W2D_LAUNCHED("double-float two-step kernel launch");
+    return WAVE2D_OK;
+}
+
+}  // namespace w2d

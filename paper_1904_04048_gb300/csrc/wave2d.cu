@@ -361,6 +361,8 @@ static int launch_simple_step(wave2d* h, bool track) {
     const ExactTab ex = track ? make_tab(h, h->tab_track, h->track_ex, (double)(h->k + 1) * h->tau) : ExactTab{};
     const Reduce rd = make_reduce(h, h->acc_track, 1);
     if (h->nclass > 0) return chain_simple_step(h, track, ex, rd);
+    // FP32x2 without per-step norms: the packed two-node kernel (same result)
+    if (h->dtype == DT_F32X2 && !track) return df2_simple_step(h, coef_as<df>(h->a));
     dispatch_dt(h->dtype, [&](auto DTc) {
         constexpr int DT = decltype(DTc)::value;
         using V = typename St<DT>::V;

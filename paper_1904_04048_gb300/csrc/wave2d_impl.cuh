@@ -137,6 +137,9 @@ void chain_tma_box(const wave2d* h, int& box_w, int& box_h, int& tile_w, int& ti
 // (rings_stale); stream_fresh_rings rebuilds them and must run before any
 // other kernel reads the planes' rings and before a library call returns.
 int stream_launch(wave2d* h);
+// One two-step of a double-float (FP32x2) Section 6 handle, two nodes per
+// thread in packed arithmetic (df2.cu); equal to k2_simple's result.
+int df2_simple_step(wave2d* h, const Coef3<df>& a);
 int stream_fresh_rings(wave2d* h);
 // Guard-band canaries (canary.cu): fill the untouched cells of every plane
 // when the handle has WAVE2D_CANARY.
