@@ -100,62 +100,78 @@ __device__ __forceinline__ df at(const Row6& r, int d) {
 
 }  // namespace
 
+// Rows per thread and the block shape of k2_df2.
+constexpr int kDf2Rows = 8;
+constexpr int kDf2BlockY = 4;
+
+// Thread (x, y) updates the node pair (i, i + 1), i = 2 (32 blockIdx.x + x),
+// on kDf2Rows consecutive rows, walking down with the 2R + 1 rows of u^k
+// around the current one in registers: each step loads one new row (the one
+// R + 1 below the next, issued before the current row's arithmetic), so
+// every row of u^k is read once per thread instead of 2R + 1 times.
 template <int S, int BCM>
-__global__ void __launch_bounds__(256) k2_df2(Level cur, Level nxt, Geo g, Coef3<df> a, int gw) {
+__global__ void __launch_bounds__(32 * kDf2BlockY) k2_df2(Level cur, Level nxt, Geo g, Coef3<df> a, int gw) {
+    constexpr int R = (S == 13) ? 2 : 1;
+    constexpr int W = 2 * R + 1;
     const int i0 = 2 * (blockIdx.x * 32 + threadIdx.x);
-    const int j = blockIdx.y * 8 + threadIdx.y;
-    if (i0 >= g.nx || j >= g.ny) return;
+    const int j0 = (blockIdx.y * kDf2BlockY + threadIdx.y) * kDf2Rows;
+    if (i0 >= g.nx || j0 >= g.ny) return;
     const bool two = i0 + 1 < g.nx;  // an odd row width leaves the last pair one node
-    const size_t o = off(g, i0, j);   // i0 + G even: 8-byte aligned pairs
     const size_t P = (size_t)g.pitch;
-
-    const Row6 C = ld_row6(cur, o);
-    const df2 c = C.c;
-    const df2 m4c = df2_scale(c, -4.0f);
-    // class (1,0): (e + w) + (n + s), then -4 u_ij
-    const df2 ew = pack(df_add(at(C, 1), at(C, -1)), df_add(at(C, 2), at(C, 0)));
-    df2 nrow, srow;
-    Row6 N, Sr;
-    if constexpr (S >= 9) {
-        N = ld_row6(cur, o + P);
-        Sr = ld_row6(cur, o - P);
-        nrow = N.c;
-        srow = Sr.c;
-    } else {
-        nrow = ldp(cur, o + P);
-        srow = ldp(cur, o - P);
-    }
-    const df2 d10 = df2_add(df2_add(ew, df2_add(nrow, srow)), m4c);
-    df2 L = df2_mul(dup2(a.a10.hi), dup2(-a.a10.hi), dup2(a.a10.lo), d10);
-    if constexpr (S >= 9) {
-        // class (1,1): (ne + sw) + (nw + se)
-        const df2 nesw = pack(df_add(at(N, 1), at(Sr, -1)), df_add(at(N, 2), at(Sr, 0)));
-        const df2 nwse = pack(df_add(at(N, -1), at(Sr, 1)), df_add(at(N, 0), at(Sr, 2)));
-        const df2 d11 = df2_add(df2_add(nesw, nwse), m4c);
-        L = df2_add(df2_mul(dup2(a.a11.hi), dup2(-a.a11.hi), dup2(a.a11.lo), d11), L);
-    }
-    if constexpr (S == 13) {
-        // class (2,0): (ee + ww) + (nn + ss)
-        const df2 nn = ldp(cur, o + 2 * P), ss = ldp(cur, o - 2 * P);
-        const df2 d20 = df2_add(df2_add(df2_add(C.p, C.m), df2_add(nn, ss)), m4c);
-        L = df2_add(df2_mul(dup2(a.a20.hi), dup2(-a.a20.hi), dup2(a.a20.lo), d20), L);
-    }
-    // u^{k-1} from the plane this thread overwrites with u^{k+1}: plain loads
-    const df2 prev = {*reinterpret_cast<const unsigned long long*>((const float*)nxt.hi + o),
-                      *reinterpret_cast<const unsigned long long*>((const float*)nxt.lo + o)};
-    const df2 r = df2_add(df2_sub(df2_scale(c, 2.0f), prev), L);
-
-    const df r0 = lane(r, 0), r1 = lane(r, 1);
-    if (two) {
-        *reinterpret_cast<unsigned long long*>((float*)nxt.hi + o) = r.hi;
-        *reinterpret_cast<unsigned long long*>((float*)nxt.lo + o) = r.lo;
-    } else {
-        ((float*)nxt.hi)[o] = r0.hi;
-        ((float*)nxt.lo)[o] = r0.lo;
-    }
-    if constexpr (BCM != BCM_ZERO) {
-        write_images_bc<DT_F32X2, BCM>(nxt, g, i0, j, r0, gw);
-        if (two) write_images_bc<DT_F32X2, BCM>(nxt, g, i0 + 1, j, r1, gw);
+    size_t o = off(g, i0, j0);        // i0 + G even: 8-byte aligned pairs
+    const f2x a10h = dup2(a.a10.hi), a10n = dup2(-a.a10.hi), a10l = dup2(a.a10.lo);
+    const f2x a11h = dup2(a.a11.hi), a11n = dup2(-a.a11.hi), a11l = dup2(a.a11.lo);
+    const f2x a20h = dup2(a.a20.hi), a20n = dup2(-a.a20.hi), a20l = dup2(a.a20.lo);
+    Row6 win[W];  // rows j - R .. j + R of u^k (rows at most kDf2Rows + R past the grid: ghost ring)
+#pragma unroll
+    for (int r = 0; r < W; ++r) win[r] = ld_row6(cur, (size_t)((ptrdiff_t)o + (ptrdiff_t)(r - R) * (ptrdiff_t)P));
+#pragma unroll
+    for (int k = 0; k < kDf2Rows; ++k) {
+        const int j = j0 + k;
+        if (j >= g.ny) break;
+        Row6 ahead;
+        if (k + 1 < kDf2Rows) ahead = ld_row6(cur, o + (size_t)(R + 1) * P);  // row j + R + 1
+        const Row6& C = win[R];
+        const Row6& N = win[R + 1];
+        const Row6& Sr = win[R - 1];
+        const df2 c = C.c;
+        const df2 m4c = df2_scale(c, -4.0f);
+        // class (1,0): (e + w) + (n + s), then -4 u_ij
+        const df2 ew = pack(df_add(at(C, 1), at(C, -1)), df_add(at(C, 2), at(C, 0)));
+        const df2 d10 = df2_add(df2_add(ew, df2_add(N.c, Sr.c)), m4c);
+        df2 L = df2_mul(a10h, a10n, a10l, d10);
+        if constexpr (S >= 9) {
+            // class (1,1): (ne + sw) + (nw + se)
+            const df2 nesw = pack(df_add(at(N, 1), at(Sr, -1)), df_add(at(N, 2), at(Sr, 0)));
+            const df2 nwse = pack(df_add(at(N, -1), at(Sr, 1)), df_add(at(N, 0), at(Sr, 2)));
+            const df2 d11 = df2_add(df2_add(nesw, nwse), m4c);
+            L = df2_add(df2_mul(a11h, a11n, a11l, d11), L);
+        }
+        if constexpr (S == 13) {
+            // class (2,0): (ee + ww) + (nn + ss)
+            const df2 d20 = df2_add(df2_add(df2_add(C.p, C.m), df2_add(win[R + 2].c, win[R - 2].c)), m4c);
+            L = df2_add(df2_mul(a20h, a20n, a20l, d20), L);
+        }
+        // u^{k-1} from the plane this thread overwrites with u^{k+1}: plain loads
+        const df2 prev = {*reinterpret_cast<const unsigned long long*>((const float*)nxt.hi + o),
+                          *reinterpret_cast<const unsigned long long*>((const float*)nxt.lo + o)};
+        const df2 r = df2_add(df2_sub(df2_scale(c, 2.0f), prev), L);
+        const df r0 = lane(r, 0), r1 = lane(r, 1);
+        if (two) {
+            *reinterpret_cast<unsigned long long*>((float*)nxt.hi + o) = r.hi;
+            *reinterpret_cast<unsigned long long*>((float*)nxt.lo + o) = r.lo;
+        } else {
+            ((float*)nxt.hi)[o] = r0.hi;
+            ((float*)nxt.lo)[o] = r0.lo;
+        }
+        if constexpr (BCM != BCM_ZERO) {
+            write_images_bc<DT_F32X2, BCM>(nxt, g, i0, j, r0, gw);
+            if (two) write_images_bc<DT_F32X2, BCM>(nxt, g, i0 + 1, j, r1, gw);
+        }
+#pragma unroll
+        for (int r2 = 0; r2 + 1 < W; ++r2) win[r2] = win[r2 + 1];
+        if (k + 1 < kDf2Rows) win[W - 1] = ahead;
+        o += P;
     }
 }
 
@@ -164,19 +180,19 @@ static void launch_df2_s(wave2d* h, const Coef3<df>& a, dim3 grid) {
     const Level cur = h->level(h->cur), nxt = h->level(h->prv);
     switch (h->bc) {
         case WAVE2D_BC_PERIODIC:
-            k2_df2<S, BCM_PERIODIC><<<grid, dim3(32, 8), 0, h->stream>>>(cur, nxt, h->geo(), a, h->gw);
+            k2_df2<S, BCM_PERIODIC><<<grid, dim3(32, kDf2BlockY), 0, h->stream>>>(cur, nxt, h->geo(), a, h->gw);
             break;
         case WAVE2D_BC_ODD:
-            k2_df2<S, BCM_ODD><<<grid, dim3(32, 8), 0, h->stream>>>(cur, nxt, h->geo(), a, h->gw);
+            k2_df2<S, BCM_ODD><<<grid, dim3(32, kDf2BlockY), 0, h->stream>>>(cur, nxt, h->geo(), a, h->gw);
             break;
         default:
-            k2_df2<S, BCM_ZERO><<<grid, dim3(32, 8), 0, h->stream>>>(cur, nxt, h->geo(), a, h->gw);
+            k2_df2<S, BCM_ZERO><<<grid, dim3(32, kDf2BlockY), 0, h->stream>>>(cur, nxt, h->geo(), a, h->gw);
             break;
     }
 }
 
 int df2_simple_step(wave2d* h, const Coef3<df>& a) {
-    const dim3 grid((((h->nx + 1) / 2) + 31) / 32, (h->ny + 7) / 8);
+    const dim3 grid((((h->nx + 1) / 2) + 31) / 32, (h->ny + kDf2BlockY * kDf2Rows - 1) / (kDf2BlockY * kDf2Rows));
     switch (h->scheme) {
         case 5: launch_df2_s<5>(h, a, grid); break;
         case 9: launch_df2_s<9>(h, a, grid); break;
