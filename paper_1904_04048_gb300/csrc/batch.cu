@@ -130,13 +130,13 @@ struct StreamInst {
 };
 
 template <int S, int T>
-__global__ void __launch_bounds__(kStreamWarps * 32)
+__global__ void __launch_bounds__(kBatchStreamWarps * 32)
     k7_batch_stream(const StreamInst* __restrict__ insts, const int* __restrict__ strip_prefix, int n_active, int q,
                     int L) {
     constexpr int NB = StreamCfg<S, T>::NB;
     extern __shared__ float4 stream_smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int strip = blockIdx.x * kStreamWarps + warp;
+    const int strip = blockIdx.x * kBatchStreamWarps + warp;
     if (strip >= __ldg(strip_prefix + n_active)) return;  // whole warps only
     int lo = 0, hi = n_active;  // strip_prefix[lo] <= strip < strip_prefix[lo + 1]
     while (hi - lo > 1) {
@@ -558,7 +558,7 @@ int build_stream_plan(wave2d_batch* b, const int64_t* steps) {
             if (!tb.nq.empty())
                 while (active > 0 && tb.nq[active - 1] <= q) --active;
             if (active == 0) break;
-            const int grid = (tb.prefix[active] + kStreamWarps - 1) / kStreamWarps;
+            const int grid = (tb.prefix[active] + kBatchStreamWarps - 1) / kBatchStreamWarps;
             b->plan_slaunches.push_back({tb.scheme, tb.T, grid, active, (int)q, tb.branch, di, dp});
         }
     }
@@ -569,24 +569,24 @@ template <int S>
 cudaError_t launch_k7(const wave2d_batch::SLaunch& l, int L, cudaStream_t st) {
     if constexpr (S != 13) {
         if (l.T == 5) {
-            k7_batch_stream<S, 5><<<l.grid, kStreamWarps * 32, stream_smem_bytes<S, 5>(), st>>>(
+            k7_batch_stream<S, 5><<<l.grid, kBatchStreamWarps * 32, stream_smem_bytes<S, 5, kBatchStreamWarps>(), st>>>(
                 (const StreamInst*)l.insts, l.prefix, l.n_active, l.q, L);
             return cudaGetLastError();
         }
         if (l.T == 6) {
-            k7_batch_stream<S, 6><<<l.grid, kStreamWarps * 32, stream_smem_bytes<S, 6>(), st>>>(
+            k7_batch_stream<S, 6><<<l.grid, kBatchStreamWarps * 32, stream_smem_bytes<S, 6, kBatchStreamWarps>(), st>>>(
                 (const StreamInst*)l.insts, l.prefix, l.n_active, l.q, L);
             return cudaGetLastError();
         }
     }
     switch (l.T) {
-        case 1: k7_batch_stream<S, 1><<<l.grid, kStreamWarps * 32, stream_smem_bytes<S, 1>(), st>>>(
+        case 1: k7_batch_stream<S, 1><<<l.grid, kBatchStreamWarps * 32, stream_smem_bytes<S, 1, kBatchStreamWarps>(), st>>>(
                     (const StreamInst*)l.insts, l.prefix, l.n_active, l.q, L); break;
-        case 2: k7_batch_stream<S, 2><<<l.grid, kStreamWarps * 32, stream_smem_bytes<S, 2>(), st>>>(
+        case 2: k7_batch_stream<S, 2><<<l.grid, kBatchStreamWarps * 32, stream_smem_bytes<S, 2, kBatchStreamWarps>(), st>>>(
                     (const StreamInst*)l.insts, l.prefix, l.n_active, l.q, L); break;
-        case 3: k7_batch_stream<S, 3><<<l.grid, kStreamWarps * 32, stream_smem_bytes<S, 3>(), st>>>(
+        case 3: k7_batch_stream<S, 3><<<l.grid, kBatchStreamWarps * 32, stream_smem_bytes<S, 3, kBatchStreamWarps>(), st>>>(
                     (const StreamInst*)l.insts, l.prefix, l.n_active, l.q, L); break;
-        default: k7_batch_stream<S, 4><<<l.grid, kStreamWarps * 32, stream_smem_bytes<S, 4>(), st>>>(
+        default: k7_batch_stream<S, 4><<<l.grid, kBatchStreamWarps * 32, stream_smem_bytes<S, 4, kBatchStreamWarps>(), st>>>(
                     (const StreamInst*)l.insts, l.prefix, l.n_active, l.q, L); break;
     }
     return cudaGetLastError();
