@@ -100,17 +100,17 @@ __device__ __forceinline__ df at(const Row6& r, int d) {
 
 }  // namespace
 
-// Rows per thread and the block shape of k2_df2.
-constexpr int kDf2Rows = 8;
+// Block shape of k2_df2 (32 x kDf2BlockY threads).
 constexpr int kDf2BlockY = 4;
 
 // Thread (x, y) updates the node pair (i, i + 1), i = 2 (32 blockIdx.x + x),
-// on kDf2Rows consecutive rows, walking down with the 2R + 1 rows of u^k
+// on K consecutive rows, walking down with the 2R + 1 rows of u^k
 // around the current one in registers: each step loads one new row (the one
 // R + 1 below the next, issued before the current row's arithmetic), so
 // every row of u^k is read once per thread instead of 2R + 1 times.
-template <int S, int BCM>
+template <int S, int BCM, int K>
 __global__ void __launch_bounds__(32 * kDf2BlockY) k2_df2(Level cur, Level nxt, Geo g, Coef3<df> a, int gw) {
+    constexpr int kDf2Rows = K;
     constexpr int R = (S == 13) ? 2 : 1;
     constexpr int W = 2 * R + 1;
     const int i0 = 2 * (blockIdx.x * 32 + threadIdx.x);
@@ -175,28 +175,42 @@ __global__ void __launch_bounds__(32 * kDf2BlockY) k2_df2(Level cur, Level nxt, 
     }
 }
 
-template <int S>
-static void launch_df2_s(wave2d* h, const Coef3<df>& a, dim3 grid) {
+template <int S, int K>
+static void launch_df2_sk(wave2d* h, const Coef3<df>& a) {
     const Level cur = h->level(h->cur), nxt = h->level(h->prv);
+    const dim3 grid((((h->nx + 1) / 2) + 31) / 32, (h->ny + kDf2BlockY * K - 1) / (kDf2BlockY * K));
+    const dim3 block(32, kDf2BlockY);
     switch (h->bc) {
         case WAVE2D_BC_PERIODIC:
-            k2_df2<S, BCM_PERIODIC><<<grid, dim3(32, kDf2BlockY), 0, h->stream>>>(cur, nxt, h->geo(), a, h->gw);
+            k2_df2<S, BCM_PERIODIC, K><<<grid, block, 0, h->stream>>>(cur, nxt, h->geo(), a, h->gw);
             break;
         case WAVE2D_BC_ODD:
-            k2_df2<S, BCM_ODD><<<grid, dim3(32, kDf2BlockY), 0, h->stream>>>(cur, nxt, h->geo(), a, h->gw);
+            k2_df2<S, BCM_ODD, K><<<grid, block, 0, h->stream>>>(cur, nxt, h->geo(), a, h->gw);
             break;
         default:
-            k2_df2<S, BCM_ZERO><<<grid, dim3(32, kDf2BlockY), 0, h->stream>>>(cur, nxt, h->geo(), a, h->gw);
+            k2_df2<S, BCM_ZERO, K><<<grid, block, 0, h->stream>>>(cur, nxt, h->geo(), a, h->gw);
             break;
     }
 }
 
+// Rows per thread: the most of 8, 4, 2 and 1 that still gives every SM 16
+// warps (a walk of 8 rows at 512^2 would leave most SMs without a warp).
+template <int S>
+static void launch_df2_s(wave2d* h, const Coef3<df>& a) {
+    const long long warps_x = (((long long)h->nx + 1) / 2 + 31) / 32;
+    const long long want = 16LL * h->num_sms;
+    auto warps = [&](int k) { return warps_x * (((long long)h->ny + k - 1) / k); };
+    if (warps(8) >= want) launch_df2_sk<S, 8>(h, a);
+    else if (warps(4) >= want) launch_df2_sk<S, 4>(h, a);
+    else if (warps(2) >= want) launch_df2_sk<S, 2>(h, a);
+    else launch_df2_sk<S, 1>(h, a);
+}
+
 int df2_simple_step(wave2d* h, const Coef3<df>& a) {
-    const dim3 grid((((h->nx + 1) / 2) + 31) / 32, (h->ny + kDf2BlockY * kDf2Rows - 1) / (kDf2BlockY * kDf2Rows));
     switch (h->scheme) {
-        case 5: launch_df2_s<5>(h, a, grid); break;
-        case 9: launch_df2_s<9>(h, a, grid); break;
-        default: launch_df2_s<13>(h, a, grid); break;
+        case 5: launch_df2_s<5>(h, a); break;
+        case 9: launch_df2_s<9>(h, a); break;
+        default: launch_df2_s<13>(h, a); break;
     }
     W2D_LAUNCHED("double-float two-step kernel launch");
     return WAVE2D_OK;

@@ -1,12 +1,13 @@
 """Double-float (FP32x2) two-step in packed arithmetic, two nodes per thread
-(csrc/df2.cu): it must reproduce the one-node kernel bit for bit.
+(csrc/df2.cu), the kernel of FP32x2 handles above 2^22 nodes: it must
+reproduce the one-node kernel bit for bit.
 
 The one-node kernel runs when per-step norms are tracked (its reduction
 path), and the persistent kernel evaluates the same per-node arithmetic one
 node per thread; both serve as references.  Covered: the 5-, 9- and 13-point
 schemes, zero, periodic and odd boundaries, odd and even row widths (a last
-pair of one node), one- and two-column grids; and parity with the FP64
-oracle at the FP32x2 tolerance."""
+pair of one node), a grid 65 nodes wide; and parity with the FP64 oracle at
+the FP32x2 tolerance."""
 import numpy as np
 import pytest
 
@@ -42,7 +43,8 @@ def _run(w, scheme, u0, v0, h, lam, steps, bc, mode):
         return sim.get_state()
 
 
-SHAPES = [(13, 31), (64, 64), (300, 97), (1, 9), (2, 5), (257, 8)]
+# every shape above 2^22 nodes, where FP32x2 handles take the packed kernel
+SHAPES = [(2049, 2049), (4100, 1100), (65, 65536)]
 
 
 @pytest.mark.parametrize("scheme", [5, 9, 13])
@@ -50,23 +52,24 @@ SHAPES = [(13, 31), (64, 64), (300, 97), (1, 9), (2, 5), (257, 8)]
 def test_packed_equals_one_node_bitwise(w, scheme, bc):
     lam = 0.9 * LAMBDA_MAX[scheme]
     for nx, ny in SHAPES:
-        if bc == BC_PERIODIC and min(nx, ny) < 3:
-            continue  # periodic images need a few nodes across
+        assert nx * ny > 1 << 22
         u0, v0, h = smooth_ic(nx, ny, bc, seed=nx * 7 + ny + scheme)
-        a = _run(w, scheme, u0, v0, h, lam, 37, bc, "packed")
-        b = _run(w, scheme, u0, v0, h, lam, 37, bc, "tracked")
-        c = _run(w, scheme, u0, v0, h, lam, 37, bc, "persistent")
-        assert a[2] == b[2] == c[2] == 37
+        a = _run(w, scheme, u0, v0, h, lam, 13, bc, "packed")
+        b = _run(w, scheme, u0, v0, h, lam, 13, bc, "tracked")
+        c = _run(w, scheme, u0, v0, h, lam, 13, bc, "persistent")
+        assert a[2] == b[2] == c[2] == 13
         for x, y, z in zip(a[:2], b[:2], c[:2]):
             assert np.array_equal(x, y) and np.array_equal(x, z), (nx, ny)
 
 
 @pytest.mark.parametrize("scheme", [5, 9, 13])
 def test_packed_parity_with_oracle(orc, w, scheme):
-    nx, ny = 130, 70
+    """A 2100 x 2000 grid (above 2^22 nodes), 8 levels: the FP64 oracle on
+    the full grid takes a few seconds."""
+    nx, ny = 2100, 2000
     u0, v0, h = smooth_ic(nx, ny, BC_PERIODIC, seed=scheme)
     lam = 0.9 * LAMBDA_MAX[scheme]
-    steps = 60
+    steps = 8
     up, uc, _ = _run(w, scheme, u0, v0, h, lam, steps, BC_PERIODIC, "packed")
     rp, rc, _ = orc.run(scheme, u0, v0, lam, lam * h, steps, bc=BC_PERIODIC)
     for got, ref in ((uc, rc), (up, rp)):
