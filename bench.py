@@ -58,9 +58,9 @@ KSHORT = {1: "simple", 2: "tma", 3: "temporal", 4: "stream", 5: "persistent"}
 # keyed by (kernel, hash of that kernel's sources without comments, scheme,
 # rows per tile or strip, levels per launch) so that a figure is dropped once
 # the kernel or the autotuner's choice changes.
-NCU_TRAFFIC = {("k5_stream", "d2f73d373ed0d607", 9, 64, 6): 165017600 + 92277504,
-               ("k5_stream", "d2f73d373ed0d607", 13, 64, 4): 181724928 + 92143104,
-               ("k2_tma", "bac687a78661262a", 13, 0, 1): 135367424 + 20049920}
+NCU_TRAFFIC = {("k5_stream", "5d1d406f6b836821", 9, 64, 6): 164908032 + 92143616,
+               ("k5_stream", "5d1d406f6b836821", 13, 64, 4): 181641216 + 92357888,
+               ("k2_tma", "abb92c6c2c27d289", 13, 0, 1): 135369216 + 20198400}
 
 # Sources each kernel is built from (the hash keys of NCU_TRAFFIC).
 KERNEL_SOURCES = {"k2_tma": ("kernels.cuh", "stencil_ops.cuh"),
@@ -864,7 +864,9 @@ def profile_case(kernel: str, scheme: int, segment: int = 28, tile_h: int = 32, 
       k2_tma:      4 one-step launches (the first step comes before them)
       k3_temporal: 3 launches of T = 4 levels, tile_h-row tiles
       k5_stream:   3 launches of T = depth levels, tile_h-row strips
-      kc2_tma:     4 one-step launches of a derived scheme (``segment``)"""
+      kc2_tma:     4 one-step launches of a derived scheme (``segment``)
+      k2_df2:      4 one-step launches in double-float (FP32x2) storage, the
+                   packed two-node kernel (about 0.5 GB on the device)"""
     from initial_data import BC_PERIODIC, LAMBDA_MAX, pulses_and_noise
     from paper_1904_04048_gb300 import wave2d as w
     u0, v0 = pulses_and_noise(N, seed=SEED)
@@ -875,8 +877,12 @@ def profile_case(kernel: str, scheme: int, segment: int = 28, tile_h: int = 32, 
     else:
         lam = 0.9 * LAMBDA_MAX[scheme]
     flags = {"plain": 0, "sums": w.DIFF_SUMS, "form": w.DIFF_FORM}[mode]
-    with w.Wave2D(N, N, h, lam * h, scheme=scheme, bc=BC_PERIODIC, dtype=w.F32, flags=flags) as sim:
-        if kernel in ("k2_tma", "kc2_tma"):
+    dtype = w.F32X2 if kernel == "k2_df2" else w.F32
+    with w.Wave2D(N, N, h, lam * h, scheme=scheme, bc=BC_PERIODIC, dtype=dtype, flags=flags) as sim:
+        if kernel == "k2_df2":
+            sim.set_tuning(kernel=w.KERNEL_SIMPLE, use_graph=0)
+            levels = 4
+        elif kernel in ("k2_tma", "kc2_tma"):
             sim.set_tuning(kernel=w.KERNEL_TMA, use_graph=0)
             levels = 4
         elif kernel == "k5_stream":
@@ -942,7 +948,7 @@ def main():
     ap.add_argument("--ref-levels", type=int, default=4, help="time levels per scheme per reference step")
     ap.add_argument("--precision", choices=["off", "bounded", "full"], default="bounded",
                     help="plane-wave precision sweep over storage modes (see precision_cases)")
-    ap.add_argument("--profile-case", choices=["k2_tma", "k3_temporal", "k5_stream", "kc2_tma"],
+    ap.add_argument("--profile-case", choices=["k2_tma", "k3_temporal", "k5_stream", "kc2_tma", "k2_df2"],
                     help="run a short case of one kernel for a profiler capture and exit")
     ap.add_argument("--profile-scheme", type=int, choices=[5, 9, 13], default=13)
     ap.add_argument("--profile-segment", type=int, default=28, help="derived scheme for kc2_tma")

@@ -58,12 +58,12 @@ struct StreamCfg {
     static_assert(PF + 2 <= NB, "a slot is refilled two steps after its last read");
 };
 
-// Independent warps per CTA of the single-grid kernel: one, so that the SM
-// holds as many warps as its registers allow (registers are granted per
-// warp; at 118 registers 17 warps fit, where CTAs of four warps stop at 16:
-// measured on GB300 at 4096^2, 13-point level 17.3 -> 17.0 us, difference
-// form 23.5 -> 22.7; the 9-point kernel unchanged).  The batched kernel keeps
-// CTAs of four warps.
+// Independent warps per CTA of the single-grid kernel: one.  The registers
+// still hold 16 warps per SM (4 per scheduler partition), but single-warp
+// CTAs are placed one warp at a time, so the SMs fill evenly (measured on
+// GB300 at 4096^2: 13-point level 17.3 -> 17.0 us, difference form 23.5 ->
+// 22.7; the 9-point kernel unchanged).  The batched kernel keeps CTAs of four
+// warps.
 constexpr int kStreamWarps = 1;
 constexpr int kBatchStreamWarps = 4;
 // shared memory per CTA of W warps: every warp's ring of input rows (both planes)
