@@ -369,21 +369,45 @@ def run_ours(args, rank, world, local_rank):
         else:
             one_step[s] = None
 
-    # end-to-end through the public API with host buffers (pinned), copies timed
+    # End to end through the public API with host buffers (pinned), copies
+    # timed: one handle per scheme on its own stream (the same tuning as the
+    # timed handles), so that one scheme's host -> device upload overlaps the
+    # other's stepping; every step uploads both schemes' inputs and reads both
+    # norms back.
     pu0 = torch.from_numpy(u0).pin_memory()
     pv0 = torch.from_numpy(v0).pin_memory()
+    e2e_streams = {s: torch.cuda.Stream(device=dev) for s in SCHEMES}
+    e2e_sims = {}
+    for s in SCHEMES:
+        lam = 0.9 * LAMBDA_MAX[s]
+        e2e_sims[s] = w.Wave2D(N, N, h, lam * h, scheme=s, bc=BC_PERIODIC, dtype=w.F32,
+                               stream=e2e_streams[s].cuda_stream)
+        kern = {"stream": w.KERNEL_STREAM, "temporal": w.KERNEL_TEMPORAL, "tma": w.KERNEL_TMA,
+                "simple": w.KERNEL_SIMPLE, "persistent": w.KERNEL_PERSISTENT}[tuned[s]["kernel"]]
+        e2e_sims[s].set_tuning(kernel=kern, temporal_t=tuned[s]["temporal_t"], tile_h=tuned[s]["tile_h"],
+                               ctas_per_sm=tuned[s]["ctas_per_sm"])
+
+    def e2e_step():
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        for s in SCHEMES:
+            e2e_streams[s].wait_stream(stream)   # after the L2 flush
+        for s in SCHEMES:
+            e2e_sims[s].first_step(pu0, pv0)     # host -> device copy inside the call
+            e2e_sims[s].step_n(STEPS_PER_SCHEME - 1)
+        for s in SCHEMES:
+            results[s] = e2e_sims[s].error_vs_exact()  # device -> host norms
+
+    e2e_step()  # warm-up of the new handles (staging pools, first launches)
     barrier()
     e2e_steps = max(1, args.steps)
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        with torch.cuda.stream(stream):
-            flush.zero_()
-        for s in SCHEMES:
-            sims[s].first_step(pu0, pv0)      # host -> device copy inside the call
-            sims[s].step_n(STEPS_PER_SCHEME - 1)
-            results[s] = sims[s].error_vs_exact()  # device -> host norms
+        e2e_step()
     barrier()
     e2e_elapsed = time.perf_counter() - t0
+    for s in SCHEMES:
+        e2e_sims[s].close()
 
     # Error of the benchmark's FP32 result (the last step's final level, k =
     # 2000) against an FP64 run of the same inputs and levels on the GPU (the
@@ -489,7 +513,10 @@ def run_ours(args, rank, world, local_rank):
                                     for s in SCHEMES},
         "e2e": {"value": round(e2e_value, 3), "unit": "G point-updates/s",
                 "h2d_bytes_per_step": len(SCHEMES) * 2 * 8 * N * N,
-                "d2h_bytes_per_step": len(SCHEMES) * (8 * 8 + 4)},
+                "d2h_bytes_per_step": len(SCHEMES) * (8 * 8 + 4),
+                "schedule": "one handle per scheme on its own stream: each scheme's upload and stepping "
+                            "overlap the other's (the device-timed value runs the schemes back to back on "
+                            "one stream, for the per-kernel roofline)"},
         "gpu_launches": launches,
         "one_step_kernel": ({"kernel": "k2_tma", "avg_launch_us": {str(s): round(one_step[s] * 1e6, 3) for s in SCHEMES},
                              "frac": {str(s): round(12 * N * N / one_step[s] / 1e9 / peak, 4) for s in SCHEMES},
