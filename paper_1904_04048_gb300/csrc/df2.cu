@@ -193,15 +193,17 @@ static void launch_df2_sk(wave2d* h, const Coef3<df>& a) {
     }
 }
 
-// Rows per thread: the most of 8, 4, 2 and 1 that still gives every SM 16
-// warps (a walk of 8 rows at 512^2 would leave most SMs without a warp).
+// Rows per thread: the most of 4, 2 and 1 that still gives every SM 16 warps
+// (a walk of 4 rows at 512^2 would leave most SMs without a warp).  Walks of
+// 8 rows were measured slower (13-point 141 against 127.5 us at 4096^2): the
+// unrolled body outgrows the instruction cache (ncu: no_instruction the top
+// stall).
 template <int S>
 static void launch_df2_s(wave2d* h, const Coef3<df>& a) {
     const long long warps_x = (((long long)h->nx + 1) / 2 + 31) / 32;
     const long long want = 16LL * h->num_sms;
     auto warps = [&](int k) { return warps_x * (((long long)h->ny + k - 1) / k); };
-    if (warps(8) >= want) launch_df2_sk<S, 8>(h, a);
-    else if (warps(4) >= want) launch_df2_sk<S, 4>(h, a);
+    if (warps(4) >= want) launch_df2_sk<S, 4>(h, a);
     else if (warps(2) >= want) launch_df2_sk<S, 2>(h, a);
     else launch_df2_sk<S, 1>(h, a);
 }

@@ -361,12 +361,12 @@ static int launch_simple_step(wave2d* h, bool track) {
     const ExactTab ex = track ? make_tab(h, h->tab_track, h->track_ex, (double)(h->k + 1) * h->tau) : ExactTab{};
     const Reduce rd = make_reduce(h, h->acc_track, 1);
     if (h->nclass > 0) return chain_simple_step(h, track, ex, rd);
-    // FP32x2 without per-step norms above 2^22 nodes: the packed two-node
-    // kernel (the same result; measured on GB300, 13-point: 142 against 167
-    // us per level at 4096^2, 515 against 646 at 8192^2, but 4-12 % slower
-    // at 512^2 - 2048^2, where the levels stay in L2 and the one-node
+    // FP32x2 without per-step norms above 2^20 nodes: the packed two-node
+    // kernel (the same result; measured on GB300, 13-point: 36.9 against 41.0
+    // us per level at 2048^2, 129 against 167 at 4096^2, 480 against 646 at
+    // 8192^2, but 8-12 % slower at 512^2 and 1024^2, where the one-node
     // kernel's occupancy wins)
-    if (h->dtype == DT_F32X2 && !track && (int64_t)h->nx * h->ny > (int64_t(1) << 22))
+    if (h->dtype == DT_F32X2 && !track && (int64_t)h->nx * h->ny > (int64_t(1) << 20))
         return df2_simple_step(h, coef_as<df>(h->a));
     dispatch_dt(h->dtype, [&](auto DTc) {
         constexpr int DT = decltype(DTc)::value;

@@ -1,5 +1,5 @@
 """Double-float (FP32x2) two-step in packed arithmetic, two nodes per thread
-(csrc/df2.cu), the kernel of FP32x2 handles above 2^22 nodes: it must
+(csrc/df2.cu), the kernel of FP32x2 handles above 2^20 nodes: it must
 reproduce the one-node kernel bit for bit.
 
 The one-node kernel runs when per-step norms are tracked (its reduction
@@ -43,7 +43,7 @@ def _run(w, scheme, u0, v0, h, lam, steps, bc, mode):
         return sim.get_state()
 
 
-# every shape above 2^22 nodes, where FP32x2 handles take the packed kernel
+# every shape above 2^20 nodes, where FP32x2 handles take the packed kernel
 SHAPES = [(2049, 2049), (4100, 1100), (65, 65536)]
 
 
@@ -52,7 +52,7 @@ SHAPES = [(2049, 2049), (4100, 1100), (65, 65536)]
 def test_packed_equals_one_node_bitwise(w, scheme, bc):
     lam = 0.9 * LAMBDA_MAX[scheme]
     for nx, ny in SHAPES:
-        assert nx * ny > 1 << 22
+        assert nx * ny > 1 << 20
         u0, v0, h = smooth_ic(nx, ny, bc, seed=nx * 7 + ny + scheme)
         a = _run(w, scheme, u0, v0, h, lam, 13, bc, "packed")
         b = _run(w, scheme, u0, v0, h, lam, 13, bc, "tracked")
@@ -64,7 +64,7 @@ def test_packed_equals_one_node_bitwise(w, scheme, bc):
 
 @pytest.mark.parametrize("scheme", [5, 9, 13])
 def test_packed_parity_with_oracle(orc, w, scheme):
-    """A 2100 x 2000 grid (above 2^22 nodes), 8 levels: the FP64 oracle on
+    """A 2100 x 2000 grid (above 2^20 nodes), 8 levels: the FP64 oracle on
     the full grid takes a few seconds."""
     nx, ny = 2100, 2000
     u0, v0, h = smooth_ic(nx, ny, BC_PERIODIC, seed=scheme)
