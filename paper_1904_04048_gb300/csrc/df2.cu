@@ -6,7 +6,7 @@
 // one-node kernel spends as many issue slots again on loads, addresses and
 // moves: measured on GB300 at 4096^2, issue 78 % active with 3.8 eligible
 // warps per scheduler, 167 us per level.  Here a thread updates nodes i and
-// i + 1 of a row: every double-float operation whose operands are register
+// i + 1 of up to four consecutive rows: every double-float operation whose operands are register
 // pairs (the centre, the north/south and second-ring neighbours, the
 // coefficient products, 2u^k - u^{k-1}, the final sum) runs as packed
 // add/sub/mul/fma .rn.f32x2, one instruction for both nodes, and the rows
@@ -105,9 +105,9 @@ constexpr int kDf2BlockY = 4;
 
 // Thread (x, y) updates the node pair (i, i + 1), i = 2 (32 blockIdx.x + x),
 // on K consecutive rows, walking down with the 2R + 1 rows of u^k
-// around the current one in registers: each step loads one new row (the one
-// R + 1 below the next, issued before the current row's arithmetic), so
-// every row of u^k is read once per thread instead of 2R + 1 times.
+// around the current one in registers: each step loads one new row (row
+// j + R + 1, issued before row j's arithmetic), so a thread reads each row of
+// its walk once instead of 2R + 1 times.
 template <int S, int BCM, int K>
 __global__ void __launch_bounds__(32 * kDf2BlockY) k2_df2(Level cur, Level nxt, Geo g, Coef3<df> a, int gw) {
     constexpr int kDf2Rows = K;
@@ -122,7 +122,7 @@ __global__ void __launch_bounds__(32 * kDf2BlockY) k2_df2(Level cur, Level nxt, 
     const f2x a10h = dup2(a.a10.hi), a10n = dup2(-a.a10.hi), a10l = dup2(a.a10.lo);
     const f2x a11h = dup2(a.a11.hi), a11n = dup2(-a.a11.hi), a11l = dup2(a.a11.lo);
     const f2x a20h = dup2(a.a20.hi), a20n = dup2(-a.a20.hi), a20l = dup2(a.a20.lo);
-    Row6 win[W];  // rows j - R .. j + R of u^k (rows at most kDf2Rows + R past the grid: ghost ring)
+    Row6 win[W];  // rows j - R .. j + R of u^k (at most R + 1 rows past the grid: the ghost ring)
 #pragma unroll
     for (int r = 0; r < W; ++r) win[r] = ld_row6(cur, (size_t)((ptrdiff_t)o + (ptrdiff_t)(r - R) * (ptrdiff_t)P));
 #pragma unroll
