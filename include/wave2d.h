@@ -150,7 +150,10 @@ typedef struct wave2d *wave2d_t;
  * and class chains of one to three classes), else the TMA kernel. */
 enum {
     WAVE2D_KERNEL_AUTO = 0,
-    WAVE2D_KERNEL_SIMPLE = 1,   /* one thread per node, global loads            */
+    WAVE2D_KERNEL_SIMPLE = 1,   /* one thread per node, global loads (FP32x2
+                                   above 2^20 nodes without per-step norms: two
+                                   nodes per thread in packed double-float
+                                   arithmetic, the same result)              */
     WAVE2D_KERNEL_TMA = 2,      /* TMA-staged shared-memory tiles, one step      */
     WAVE2D_KERNEL_TEMPORAL = 3, /* TMA tiles advanced T steps in shared memory   */
     WAVE2D_KERNEL_STREAM = 4,   /* T steps per launch with the levels in
