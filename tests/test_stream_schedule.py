@@ -83,3 +83,63 @@ def test_first_valid_rows_are_the_halo_bound():
             for t in range(1, T + 1):
                 first_step = t * (D + R)
                 assert rho0 + first_step - t * D == rho0 + t * R
+
+
+def replay_strip_difference_form(R, T, L, y0=0):
+    """The difference form's schedule: level t on row r = rho - t D takes
+    d^{t-1} of row r from the d row level t - 1 computed D steps earlier
+    (a second ring per level, slot (r - rho0) mod (2D + 1)), or for t = 1
+    the d^k row loaded with the step (the prev plane's row rho - D); the
+    stored rows are u^{k+T} and d^{k+T} of the strip's output rows."""
+    D = R
+    WIN = 2 * D + 1
+    rho0 = y0 - R * T
+    nsteps = L + T * (D + R)
+    ring = [[None] * WIN for _ in range(T)]      # u rows of levels 0 .. T-1
+    ringd = [[None] * WIN for _ in range(T)]     # d rows of levels 1 .. T-1 (index 0 unused)
+    valid = [set() for _ in range(T + 1)]
+    valid_d = [set() for _ in range(T + 1)]
+    stored = []
+    for base in range(0, nsteps, WIN):
+        for s in range(WIN):
+            step = base + s
+            if step >= nsteps:
+                break
+            rho = rho0 + step
+            ring[0][s] = rho
+            valid[0].add(rho)
+            pm = rho - D                          # d^k row loaded with this step
+            valid_d[0].add(pm)
+            top = dtop = None
+            for t in range(1, T + 1):
+                if step < t * (D + R):
+                    continue
+                r = rho - t * D
+                cs = (s - t * D) % WIN
+                window = [ring[t - 1][(cs + d) % WIN] for d in range(-R, R + 1)]
+                assert window == [r + d for d in range(-R, R + 1)], (t, step, window)
+                dprev = pm if t == 1 else ringd[t - 1][cs]
+                assert dprev == r, (t, step, dprev, r)
+                if all(y in valid[t - 1] for y in window) and r in valid_d[t - 1]:
+                    valid[t].add(r)
+                    valid_d[t].add(r)
+                if t < T:
+                    ring[t][cs] = r
+                    ringd[t][cs] = r
+                else:
+                    top = dtop = r
+            if step < T * (D + R):
+                continue
+            ro = rho - T * D
+            assert top == ro and dtop == ro
+            assert ro in valid[T] and ro in valid_d[T]
+            stored.append(ro)
+    assert stored == list(range(y0, y0 + L))
+
+
+@pytest.mark.parametrize("R", [1, 2])
+@pytest.mark.parametrize("T", [2, 3, 4])
+@pytest.mark.parametrize("L", [8, 9, 16, 17, 37, 64])
+def test_ring_schedule_difference_form(R, T, L):
+    replay_strip_difference_form(R, T, L)
+    replay_strip_difference_form(R, T, L, y0=3 * L)
