@@ -882,6 +882,58 @@ def measure_diff_sums(w, torch, u0, v0, peak, plain_us=None):
     return out
 
 
+def measure_slabs(n: int = 8192, scheme: int = 13, levels: int = 400, T: int = 4):
+    """Row-slab decomposition of one grid (paper_1904_04048_gb300/slab.py),
+    all slabs on this GPU: an n^2 periodic grid, FP32, the streaming kernel
+    (T levels per launch, 64-row strips), split into P = 1 (the undivided
+    handle), 2, 4 and 8 slabs that exchange their R T halo rows (both
+    planes, device buffers) after every T levels.  Host wall clock over
+    ``levels`` levels after the first step and a warm-up of 2 T levels; the
+    slabs advance one after another on the default stream (row copies
+    stream-ordered, no host wait per exchange), so the figure is the
+    decomposition's cost on one device (halo recomputation, row copies, the
+    host's launch work per slab), not a multi-GPU speed."""
+    import torch
+    from initial_data import BC_PERIODIC, LAMBDA_MAX, pulses_and_noise
+    from paper_1904_04048_gb300 import slab
+    from paper_1904_04048_gb300 import wave2d as w
+    u0, v0 = pulses_and_noise(n, seed=SEED)
+    h = 1.0 / n
+    lam = 0.9 * LAMBDA_MAX[scheme]
+    R = 2 if scheme == 13 else 1
+    tune = dict(kernel=w.KERNEL_STREAM, temporal_t=T, tile_h=64, use_graph=0)
+    out = {}
+    for P in (1, 2, 4, 8):
+        sims, runs = [], []
+        try:
+            for r in range(P):
+                plan = slab.plan_slabs(n, n, P, r, R, T, True)
+                sim = w.Wave2D(n, plan.ny_local, h, lam * h, scheme=scheme, bc=BC_PERIODIC, dtype=w.F32)
+                sim.set_tuning(**tune)
+                sims.append(sim)
+                runs.append(slab.SlabRun(plan, slab.HandleSolver(sim), device=torch.device("cuda")))
+            exch = slab.LocalExchange(sync=False)  # every handle and buffer on the default stream
+            slab.first_step(runs, exch, [slab.extended_rows(r.plan, u0) for r in runs],
+                            [slab.extended_rows(r.plan, v0) for r in runs])
+            slab.step_n(runs, exch, 2 * T)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            slab.step_n(runs, exch, levels)
+            torch.cuda.synchronize()
+            sec = time.perf_counter() - t0
+        finally:
+            for sim in sims:
+                sim.close()
+        out[str(P)] = {"ms": round(sec * 1e3, 2), "value": round(n * n * levels / sec / 1e9, 1),
+                       "unit": "G point-updates/s", "halo_rows_per_slab": 2 * R * T if P > 1 else 0}
+    base = out["1"]["value"]
+    for v in out.values():
+        v["vs_undivided"] = round(v["value"] / base, 3)
+    return {"workload": f"{n}^2 periodic, {scheme}-point, FP32, streaming T = {T}, 64-row strips, {levels} "
+                        f"levels, slabs exchanging halo rows every T levels, all on one GPU",
+            "slabs": out}
+
+
 def profile_case(kernel: str, scheme: int, segment: int = 28, tile_h: int = 32, depth: int = 4,
                  mode: str = "plain"):
     """A short run of one kernel at the benchmark size, for profiler captures:
@@ -983,7 +1035,12 @@ def main():
     ap.add_argument("--profile-depth", type=int, default=4, help="levels per launch of k5_stream")
     ap.add_argument("--profile-mode", choices=["plain", "sums", "form"], default="plain",
                     help="storage and arithmetic: plain sums, WAVE2D_DIFF_SUMS or WAVE2D_DIFF_FORM")
+    ap.add_argument("--slab-probe", action="store_true",
+                    help="measure the row-slab decomposition of one 8192^2 grid on this GPU (one JSON line)")
     args = ap.parse_args()
+    if args.slab_probe:
+        print(json.dumps(measure_slabs()))
+        return
     if args.profile_case:
         profile_case(args.profile_case, args.profile_scheme, args.profile_segment, args.profile_tile,
                      args.profile_depth, args.profile_mode)

@@ -170,14 +170,17 @@ class SlabRun:
         td = torch.float64 if self._np_dtype == np.float64 else torch.float32
         return torch.empty(self._msg_shape, dtype=td, device=self.device)
 
-    def outgoing(self):
-        """Pack the rows this slab sends: [(peer, tag, tensor of both planes)]."""
+    def outgoing(self, sync=True):
+        """Pack the rows this slab sends: [(peer, tag, tensor of both planes)].
+        ``sync``: wait for the copies (another stream, a communication
+        library or the host reads the buffers next)."""
         out = []
         for peer, tag, j0 in self.plan.sends():
             buf = self._buffer()
             self.solver.get_rows(j0, self.plan.H, buf[0], buf[1])
             out.append((peer, tag, buf))
-        self.solver.sync()  # device copies done before another stream reads them
+        if sync:
+            self.solver.sync()  # device copies done before another stream reads them
         return out
 
     def incoming(self):
@@ -272,12 +275,20 @@ class DistExchange:
 class LocalExchange:
     """The same exchange among all slabs of a grid held by one process (for
     example every slab on one GPU): messages are matched by (sender,
-    receiver, tag) in posting order and copied directly."""
+    receiver, tag) in posting order and copied directly.
+
+    ``sync=False`` when every slab's solver launches on the stream that
+    allocates the message buffers (every handle and torch on the default
+    stream of one device): the row copies are then ordered by that stream and
+    the exchange waits for nothing on the host."""
+
+    def __init__(self, sync=True):
+        self.sync = sync
 
     def run(self, runs):
         mail = {}
         for r in runs:
-            for peer, tag, buf in r.outgoing():
+            for peer, tag, buf in r.outgoing(sync=self.sync):
                 mail.setdefault((r.plan.rank, peer, tag), []).append(buf)
         for r in runs:
             got = [(peer, tag, mail[(peer, r.plan.rank, tag)].pop(0)) for peer, tag, _ in r.plan.recvs()]

@@ -44,7 +44,8 @@ def _ic(nx, ny, bc, seed):
 @pytest.mark.parametrize("bc", [BC_ZERO, BC_PERIODIC], ids=["zero", "periodic"])
 @pytest.mark.parametrize("dtype", [0, 1, 2], ids=["f64", "f32", "f32x2"])
 @pytest.mark.parametrize("world,T,kernel", [(2, 4, "stream"), (3, 6, "auto"), (4, 3, "tma")])
-def test_slabs_on_one_gpu_equal_the_undivided_handle(w, scheme, bc, dtype, world, T, kernel):
+@pytest.mark.parametrize("sync", [True, False], ids=["sync", "stream-ordered"])
+def test_slabs_on_one_gpu_equal_the_undivided_handle(w, scheme, bc, dtype, world, T, kernel, sync):
     import torch
     from paper_1904_04048_gb300 import slab
     nx, ny, n_t = 200, 131, 40
@@ -72,7 +73,7 @@ def test_slabs_on_one_gpu_equal_the_undivided_handle(w, scheme, bc, dtype, world
             sims.append(sim)
             sim.set_tuning(**tune)
             runs.append(slab.SlabRun(plan, slab.HandleSolver(sim), device=torch.device("cuda")))
-        exch = slab.LocalExchange()
+        exch = slab.LocalExchange(sync=sync)  # handles and buffers share the default stream
         slab.first_step(runs, exch, [slab.extended_rows(r.plan, u0) for r in runs],
                         [slab.extended_rows(r.plan, v0) for r in runs])
         slab.step_n(runs, exch, n_t - 1)
